@@ -1,0 +1,187 @@
+"""FP64 CPU oracle for the two-scale DD Eikonal method (arXiv:1805.04198).
+
+TEST INFRASTRUCTURE ONLY.  The test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may load it; the product path never does.  It
+shares no code with the CUDA library: the C source here is compiled on its own
+with ``-ffp-contract=off`` so that no multiply-add is fused.
+
+Functions (each follows the paper section named in its docstring):
+  local_solve  Godunov local solve, Sec. 1.1 eq. (godonuv) / Alg. 3
+  fsm          fast sweeping method, Sec. 1.1
+  fmm          Dijkstra/fast marching on the same discrete system (Sec. 1.1)
+  dd           two-scale domain decomposition, Sec. 3.2 Steps 1-4, Alg. 1-5
+  adjoint      discrete adjoint of the converged Godunov system (no paper
+               counterpart; checked by finite differences)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "eik_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (serial FP64, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class DDParams(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_long * 3), ("h", ctypes.c_double),
+                ("tiles", ctypes.c_int * 3), ("c", ctypes.c_int), ("theta", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_fsm_sweeps", ctypes.c_long), ("max_coarse_sweeps", ctypes.c_long)]
+
+
+class DDStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("last_delta", ctypes.c_double),
+                ("fsm_sweeps_max", ctypes.c_long), ("coarse_sweeps_max", ctypes.c_long),
+                ("fsm_cap_hits", ctypes.c_long), ("coarse_cap_hits", ctypes.c_long),
+                ("causal_rounds_max", ctypes.c_long)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            bp = ctypes.POINTER(ctypes.c_ubyte)
+            sp = ctypes.POINTER(ctypes.c_byte)
+            lp = ctypes.POINTER(ctypes.c_long)
+            lib.orc_local_solve.restype = ctypes.c_double
+            lib.orc_local_solve.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, sp]
+            lib.orc_fsm.restype = ctypes.c_long
+            lib.orc_fsm.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, sp, ctypes.c_long,
+                                    ctypes.POINTER(ctypes.c_int)]
+            lib.orc_fmm.restype = None
+            lib.orc_fmm.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp]
+            lib.orc_dd.restype = ctypes.c_int
+            lib.orc_dd.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, dp, dp, ctypes.POINTER(DDStats)]
+            lib.orc_adjoint.restype = None
+            lib.orc_adjoint.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, dp]
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _bp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+
+
+def _sp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_byte))
+
+
+def _shape_n(shape):
+    """numpy shape (z, y, x) / (y, x) -> (d, n[3]) with n[0] = x extent."""
+    d = len(shape)
+    n = list(reversed(shape)) + [1] * (3 - d)
+    return d, (ctypes.c_long * 3)(*n)
+
+
+def _prep(r, gamma, g):
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    gamma = np.ascontiguousarray(gamma, dtype=np.uint8)
+    g = np.ascontiguousarray(np.broadcast_to(g, r.shape), dtype=np.float64)
+    assert r.shape == gamma.shape
+    return r, gamma, g
+
+
+def local_solve(vm, vp, rh):
+    """Godunov local solve (Sec. 1.1 / Alg. 3).  Returns (u~, wind tuple)."""
+    lib = _load()
+    d = len(vm)
+    a = np.ascontiguousarray(vm, dtype=np.float64)
+    b = np.ascontiguousarray(vp, dtype=np.float64)
+    w = np.zeros(3, dtype=np.int8)
+    u = lib.orc_local_solve(d, _dp(a), _dp(b), float(rh), _sp(w))
+    return u, tuple(int(v) for v in w[:d])
+
+
+def fsm(r, gamma, g, h, max_sweeps=100000, return_wind=False):
+    """Fast sweeping method (Sec. 1.1).  Returns (u, sweeps, converged[, wind])."""
+    lib = _load()
+    r, gamma, g = _prep(r, gamma, g)
+    d, n = _shape_n(r.shape)
+    u = np.empty_like(r)
+    w = np.zeros(r.shape + (3,), dtype=np.int8)
+    conv = ctypes.c_int(0)
+    s = lib.orc_fsm(d, n, float(h), _dp(r), _bp(gamma), _dp(g), _dp(u), _sp(w), int(max_sweeps),
+                    ctypes.byref(conv))
+    out = (u, int(s), bool(conv.value))
+    if return_wind:
+        out = out + (w[..., :d],)
+    return out
+
+
+def fmm(r, gamma, g, h):
+    """Dijkstra / fast marching on the same scheme (cross-check of fsm)."""
+    lib = _load()
+    r, gamma, g = _prep(r, gamma, g)
+    d, n = _shape_n(r.shape)
+    u = np.empty_like(r)
+    lib.orc_fmm(d, n, float(h), _dp(r), _bp(gamma), _dp(g), _dp(u))
+    return u
+
+
+def dd(r, gamma, g, h, tiles, c, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
+       max_coarse_sweeps=80, return_coarse=False):
+    """Two-scale DD iteration (Sec. 3.2, Steps 1-4).
+
+    tiles: subdomains per axis in (x, y[, z]) order.  Returns (u, stats dict,
+    delta_log[, U]) where delta_log[k] = max |U^k - U^{k-1}|.
+    """
+    lib = _load()
+    r, gamma, g = _prep(r, gamma, g)
+    d, n = _shape_n(r.shape)
+    t = list(tiles) + [1] * (3 - len(tiles))
+    p = DDParams(d, n, float(h), (ctypes.c_int * 3)(*t), int(c), float(theta), int(max_iter), float(tol),
+                 int(max_fsm_sweeps), int(max_coarse_sweeps))
+    u = np.empty_like(r)
+    U = np.empty_like(r)
+    log = np.empty(max_iter + 1, dtype=np.float64)
+    st = DDStats()
+    rc = lib.orc_dd(ctypes.byref(p), _dp(r), _bp(gamma), _dp(g), _dp(u), _dp(U), _dp(log), ctypes.byref(st))
+    if rc != 0:
+        raise ValueError("oracle dd: invalid parameters")
+    out = (u, st.as_dict(), log)
+    if return_coarse:
+        out = out + (U,)
+    return out
+
+
+def adjoint(r, gamma, u, dJdu, h):
+    """dJ/dr of the converged discrete system at u for a scalar J with dJ/du given."""
+    lib = _load()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    gamma = np.ascontiguousarray(gamma, dtype=np.uint8)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    dJdu = np.ascontiguousarray(dJdu, dtype=np.float64)
+    d, n = _shape_n(r.shape)
+    out = np.zeros_like(r)
+    lib.orc_adjoint(d, n, float(h), _dp(r), _bp(gamma), _dp(u), _dp(dJdu), _dp(out))
+    return out

@@ -1,0 +1,979 @@
+/*
+ * eik_oracle.c -- serial FP64 oracle for arXiv:1805.04198 (Martin & Tsai).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * CPU-baseline leg of bench.py; never by the product path.  Plain loops, no
+ * blocking, no fusion: each routine follows the paper's steps in the paper's
+ * order so it can be checked against the text by eye.  Build with
+ * -ffp-contract=off so no multiply-add is fused (the arithmetic below is the
+ * arithmetic the results are defined by).
+ *
+ * Readings of the paper taken here (each also listed in the design doc):
+ *  - wind signs: direction of travel everywhere (+1 when the upwind, smaller
+ *    neighbour is on the minus side); Alg. 1, 2, 4 and Step 2 are consistent
+ *    only under this sign, so Alg. 3's printed signs are read as flipped;
+ *  - Alg. 1 uses Alg. 3's branch test |a-b| < r h;
+ *  - the wind of an FSM solve is the wind of the local solve at the converged
+ *    state (path-independent; equal to the last stored wind except at exact
+ *    neighbour ties);
+ *  - an FSM (fine or coarse) stops after the first sweep that changes nothing;
+ *  - Step 2: a boundary node is Dirichlet (fixed at U) when W.n > 0 for some
+ *    inward normal n of the subdomain, otherwise free (starts at +inf and is
+ *    updated with one-sided differences); Gamma is fixed at g in every grid;
+ *    the wind of a Dirichlet node is W;
+ *  - Alg. 4 / Alg. 5 at a node lying on several coarse lines (or interfaces):
+ *    the agreement test is applied per axis and must pass on every axis;
+ *  - Alg. 5 keeps the paper's overwrite update, evaluated as
+ *    u^k + theta (U~ - C_H(U^k)); when U~ or C_H(U^k) is +inf it takes u^k;
+ *  - causal sweep (Alg. 2): repeated until nothing changes (its least fixed
+ *    point); a node is never raised to an unreached (+inf) neighbour.
+ */
+#include "eik_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define INF HUGE_VAL
+
+/* ------------------------------------------------------------------------- */
+/* Local solver: Sec. 1.1 eq. (godonuv); 2-D closed form of Sec. 3.2 (C_H) and  */
+/* Alg. 3; 3-D by the sorted-minima cascade (the paper says the 2-D method      */
+/* "can be generalized"; the 3-D Godunov solve is the standard one of its       */
+/* FSM reference).                                                              */
+/* ------------------------------------------------------------------------- */
+double orc_local_solve(int d, const double *vm, const double *vp, double rh, signed char *w)
+{
+    double a[3];
+    int s[3];
+    int k;
+    for (k = 0; k < d; ++k) {
+        /* Alg. 3: take the smaller neighbour along each axis; a tie goes to the
+         * plus-side neighbour.  Sign = direction of travel. */
+        if (vm[k] < vp[k]) {
+            a[k] = vm[k];
+            s[k] = +1;
+        } else {
+            a[k] = vp[k];
+            s[k] = -1;
+        }
+        w[k] = 0;
+    }
+    if (d == 1) {
+        double u = a[0] + rh;
+        if (u < INF) w[0] = (signed char)s[0];
+        return u;
+    }
+    if (d == 2) {
+        double u;
+        if (fabs(a[0] - a[1]) < rh) {
+            double t = a[0] - a[1];
+            u = (a[0] + a[1] + sqrt(2.0 * rh * rh - t * t)) * 0.5;
+            w[0] = (signed char)s[0];
+            w[1] = (signed char)s[1];
+        } else {
+            if (a[0] < a[1]) {
+                u = a[0] + rh;
+                if (u < INF) w[0] = (signed char)s[0];
+            } else {
+                u = a[1] + rh;
+                if (u < INF) w[1] = (signed char)s[1];
+            }
+        }
+        return u;
+    }
+    /* d == 3: order the axis minima p0 <= p1 <= p2 (ties keep axis order). */
+    {
+        int p[3] = {0, 1, 2};
+        int i, j;
+        double u;
+        for (i = 1; i < 3; ++i)
+            for (j = i; j > 0 && a[p[j]] < a[p[j - 1]]; --j) {
+                int t = p[j];
+                p[j] = p[j - 1];
+                p[j - 1] = t;
+            }
+        if (fabs(a[p[0]] - a[p[1]]) < rh) {
+            double t = a[p[0]] - a[p[1]];
+            u = (a[p[0]] + a[p[1]] + sqrt(2.0 * rh * rh - t * t)) * 0.5;
+            if (u > a[p[2]]) {
+                /* three-term quadratic in t = u - a_p0:
+                 *   t^2 + (t - d1)^2 + (t - d2)^2 = (r h)^2 */
+                double d1 = a[p[1]] - a[p[0]];
+                double d2 = a[p[2]] - a[p[0]];
+                double sd = d1 + d2;
+                double disc = sd * sd - 3.0 * (d1 * d1 + d2 * d2 - rh * rh);
+                if (disc < 0.0) disc = 0.0;
+                u = a[p[0]] + (sd + sqrt(disc)) / 3.0;
+                w[0] = (signed char)s[0];
+                w[1] = (signed char)s[1];
+                w[2] = (signed char)s[2];
+            } else {
+                w[p[0]] = (signed char)s[p[0]];
+                w[p[1]] = (signed char)s[p[1]];
+            }
+        } else {
+            u = a[p[0]] + rh;
+            if (u < INF) w[p[0]] = (signed char)s[p[0]];
+        }
+        return u;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* A "local grid": a dense box of m[0] x m[1] x m[2] nodes, spacing hs.         */
+/* Used for whole grids, for subdomains (Step 3) and for shifted coarse grids  */
+/* (Steps 1 and 4), after gathering their values into a dense local array.     */
+/* ------------------------------------------------------------------------- */
+static long lidx(const long *m, long x, long y, long z) { return x + m[0] * (y + m[1] * z); }
+
+static void nbrs(int d, const long *m, const double *u, long x, long y, long z, double *vm, double *vp)
+{
+    long c[3] = {x, y, z};
+    long st[3] = {1, m[0], m[0] * m[1]};
+    long i = lidx(m, x, y, z);
+    int k;
+    for (k = 0; k < d; ++k) {
+        vm[k] = (c[k] > 0) ? u[i - st[k]] : INF;
+        vp[k] = (c[k] < m[k] - 1) ? u[i + st[k]] : INF;
+    }
+}
+
+/* The 2^d sweep orderings of Sec. 1.1 in the printed loop order: the sign of
+ * axis 0 is the outermost loop, -1 before +1; within a sweep axis 0 is the
+ * outermost node loop.  sgn[k] receives the sign of axis k for ordering q. */
+static void ordering(int d, int q, int *sgn)
+{
+    int k;
+    for (k = 0; k < 3; ++k) sgn[k] = 1;
+    for (k = 0; k < d; ++k) sgn[k] = ((q >> (d - 1 - k)) & 1) ? +1 : -1;
+}
+
+static long start_of(long mm, int s) { return s > 0 ? 0 : mm - 1; }
+
+/* One Gauss-Seidel FSM sweep (Sec. 1.1 update u = min(u, u~)). */
+static int fsm_sweep(int d, const long *m, double hs, const double *r, const unsigned char *fixed,
+                     double *u, int q)
+{
+    int sg[3];
+    long x, y, z;
+    int changed = 0;
+    ordering(d, q, sg);
+    for (x = start_of(m[0], sg[0]); x >= 0 && x < m[0]; x += sg[0])
+        for (y = start_of(m[1], sg[1]); y >= 0 && y < m[1]; y += sg[1])
+            for (z = start_of(m[2], sg[2]); z >= 0 && z < m[2]; z += sg[2]) {
+                long i = lidx(m, x, y, z);
+                double vm[3], vp[3], ut;
+                signed char w[3];
+                if (fixed[i]) continue;
+                nbrs(d, m, u, x, y, z, vm, vp);
+                ut = orc_local_solve(d, vm, vp, r[i] * hs, w);
+                if (ut < u[i]) {
+                    u[i] = ut;
+                    changed = 1;
+                }
+            }
+    return changed;
+}
+
+/* FSM on a local grid: sweeps cycle through the orderings until one sweep
+ * changes nothing (a fixed point) or max_sweeps ran.  Returns sweeps done. */
+static long fsm_local(int d, const long *m, double hs, const double *r, const unsigned char *fixed,
+                      double *u, long max_sweeps, int *converged)
+{
+    long s = 0;
+    int nq = 1 << d;
+    *converged = 0;
+    while (s < max_sweeps) {
+        int ch = fsm_sweep(d, m, hs, r, fixed, u, (int)(s % nq));
+        ++s;
+        if (!ch) {
+            *converged = 1;
+            break;
+        }
+    }
+    return s;
+}
+
+/* Wind of the local solve at the current state (Alg. 1 / Alg. 3). */
+static void winds_local(int d, const long *m, double hs, const double *r, const unsigned char *fixed,
+                        const double *u, signed char *w)
+{
+    long x, y, z;
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long i = lidx(m, x, y, z);
+                double vm[3], vp[3];
+                signed char wt[3] = {0, 0, 0};
+                int k;
+                if (!fixed[i] && u[i] < INF) {
+                    nbrs(d, m, u, x, y, z, vm, vp);
+                    (void)orc_local_solve(d, vm, vp, r[i] * hs, wt);
+                }
+                if (!fixed[i])
+                    for (k = 0; k < 3; ++k) w[3 * i + k] = (k < d) ? wt[k] : 0;
+            }
+}
+
+long orc_fsm(int d, const long *n, double h, const double *r, const unsigned char *gamma,
+             const double *g, double *u, signed char *w, long max_sweeps, int *converged)
+{
+    long m[3] = {n[0], d > 1 ? n[1] : 1, d > 2 ? n[2] : 1};
+    long N = m[0] * m[1] * m[2], i, s;
+    /* Sec. 1.1 initialisation: Gamma fixed at g, every other node large. */
+    for (i = 0; i < N; ++i) u[i] = gamma[i] ? g[i] : INF;
+    s = fsm_local(d, m, h, r, gamma, u, max_sweeps, converged);
+    if (w) {
+        for (i = 0; i < 3 * N; ++i) w[i] = 0;
+        winds_local(d, m, h, r, gamma, u, w);
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dijkstra / FMM on the same local solver (binary heap, lazy deletion).        */
+/* ------------------------------------------------------------------------- */
+typedef struct { double v; long i; } hent;
+
+static void hpush(hent *h, long *hn, double v, long i)
+{
+    long k = (*hn)++;
+    h[k].v = v;
+    h[k].i = i;
+    while (k > 0) {
+        long p = (k - 1) / 2;
+        if (h[p].v <= h[k].v) break;
+        hent t = h[p];
+        h[p] = h[k];
+        h[k] = t;
+        k = p;
+    }
+}
+
+static hent hpop(hent *h, long *hn)
+{
+    hent top = h[0];
+    long k = 0;
+    h[0] = h[--(*hn)];
+    for (;;) {
+        long l = 2 * k + 1, rr = l + 1, b = k;
+        if (l < *hn && h[l].v < h[b].v) b = l;
+        if (rr < *hn && h[rr].v < h[b].v) b = rr;
+        if (b == k) break;
+        hent t = h[b];
+        h[b] = h[k];
+        h[k] = t;
+        k = b;
+    }
+    return top;
+}
+
+void orc_fmm(int d, const long *n, double h, const double *r, const unsigned char *gamma,
+             const double *g, double *u)
+{
+    long m[3] = {n[0], d > 1 ? n[1] : 1, d > 2 ? n[2] : 1};
+    long N = m[0] * m[1] * m[2], i;
+    long st[3] = {1, m[0], m[0] * m[1]};
+    unsigned char *acc = calloc((size_t)N, 1);
+    double *ua = malloc(sizeof(double) * (size_t)N); /* accepted values, +inf otherwise */
+    hent *hp = malloc(sizeof(hent) * (size_t)(N * 2 * d + N + 1));
+    long hn = 0;
+    for (i = 0; i < N; ++i) {
+        ua[i] = INF;
+        u[i] = INF;
+        if (gamma[i]) {
+            u[i] = g[i];
+            hpush(hp, &hn, g[i], i);
+        }
+    }
+    while (hn > 0) {
+        hent e = hpop(hp, &hn);
+        long c[3], k;
+        if (acc[e.i] || e.v != u[e.i]) continue;
+        acc[e.i] = 1;
+        ua[e.i] = u[e.i];
+        c[0] = e.i % m[0];
+        c[1] = (e.i / m[0]) % m[1];
+        c[2] = e.i / (m[0] * m[1]);
+        for (k = 0; k < d; ++k) {
+            int sd;
+            for (sd = -1; sd <= 1; sd += 2) {
+                long cc[3] = {c[0], c[1], c[2]};
+                long j;
+                double vm[3], vp[3], ut;
+                signed char w[3];
+                cc[k] += sd;
+                if (cc[k] < 0 || cc[k] >= m[k]) continue;
+                j = e.i + sd * st[k];
+                if (acc[j] || gamma[j]) continue;
+                /* tentative value from accepted neighbours only */
+                nbrs(d, m, ua, cc[0], cc[1], cc[2], vm, vp);
+                ut = orc_local_solve(d, vm, vp, r[j] * h, w);
+                if (ut < u[j]) {
+                    u[j] = ut;
+                    hpush(hp, &hn, ut, j);
+                }
+            }
+        }
+    }
+    free(acc);
+    free(ua);
+    free(hp);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Two-scale DD, Sec. 3.2.                                                      */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int d;
+    long n[3], N;
+    long st[3];
+    long S[3];
+    int T[3];
+    int c;
+} geom_t;
+
+static void coords(const geom_t *G, long i, long *x)
+{
+    x[0] = i % G->n[0];
+    x[1] = (i / G->n[0]) % G->n[1];
+    x[2] = i / (G->n[0] * G->n[1]);
+}
+
+/* Axes along which node x lies on a coarse line (index = 0 mod c). */
+static int coarse_axes(const geom_t *G, const long *x)
+{
+    int k, A = 0;
+    for (k = 0; k < G->d; ++k)
+        if (x[k] % G->c == 0) A |= 1 << k;
+    return A;
+}
+
+/* The shifted coarse grid holding node x: offset o = x mod c, spacing c
+ * (Sec. 3.2: Omega^H + (l h, 0), Omega^H + (0, m h), and their 3-D analogues).
+ * Its dense box has m[k] = (n[k]-1-o[k])/c + 1 nodes per axis. */
+static void grid_box(const geom_t *G, const long *o, long *m)
+{
+    int k;
+    for (k = 0; k < 3; ++k) m[k] = (k < G->d) ? (G->n[k] - 1 - o[k]) / G->c + 1 : 1;
+}
+
+static long grid_fine(const geom_t *G, const long *o, long x, long y, long z)
+{
+    long c = G->c;
+    long xx = o[0] + c * x, yy = (G->d > 1) ? o[1] + c * y : 0, zz = (G->d > 2) ? o[2] + c * z : 0;
+    return xx + G->n[0] * (yy + G->n[1] * zz);
+}
+
+/* Enumerate every shifted coarse grid: offsets with at least one zero. */
+static int next_offset(const geom_t *G, long *o, int first)
+{
+    for (;;) {
+        int k;
+        if (first) {
+            o[0] = o[1] = o[2] = 0;
+            first = 0;
+        } else {
+            for (k = 0; k < G->d; ++k) {
+                if (++o[k] < G->c) break;
+                o[k] = 0;
+            }
+            if (k == G->d) return 0;
+        }
+        for (k = 0; k < G->d; ++k)
+            if (o[k] == 0) return 1;
+    }
+}
+
+/* Causal sweep, Alg. 2, generalised per axis: along every axis e such that the
+ * fine neighbour x +- e_e is also on the coarse set, a node whose wind points
+ * along -e (upwind at +e) is raised to that neighbour if smaller, and the
+ * mirror case.  Passes in the 2^d orderings are repeated until nothing
+ * changes.  Returns the number of rounds. */
+static long causal_sweep(const geom_t *G, double *U, const signed char *W)
+{
+    long rounds = 0;
+    int changed;
+    do {
+        int q;
+        changed = 0;
+        ++rounds;
+        for (q = 0; q < (1 << G->d); ++q) {
+            int sg[3];
+            long x[3];
+            ordering(G->d, q, sg);
+            for (x[0] = start_of(G->n[0], sg[0]); x[0] >= 0 && x[0] < G->n[0]; x[0] += sg[0])
+                for (x[1] = start_of(G->n[1], sg[1]); x[1] >= 0 && x[1] < G->n[1]; x[1] += sg[1])
+                    for (x[2] = start_of(G->n[2], sg[2]); x[2] >= 0 && x[2] < G->n[2]; x[2] += sg[2]) {
+                        int A = coarse_axes(G, x), e;
+                        long i = x[0] + G->n[0] * (x[1] + G->n[1] * x[2]);
+                        if (!A) continue;
+                        for (e = 0; e < G->d; ++e) {
+                            if ((A & ~(1 << e)) == 0) continue;
+                            if (W[3 * i + e] < 0 && x[e] + 1 < G->n[e]) {
+                                double v = U[i + G->st[e]];
+                                if (v < INF && U[i] < v) {
+                                    U[i] = v;
+                                    changed = 1;
+                                }
+                            }
+                            if (W[3 * i + e] > 0 && x[e] > 0) {
+                                double v = U[i - G->st[e]];
+                                if (v < INF && U[i] < v) {
+                                    U[i] = v;
+                                    changed = 1;
+                                }
+                            }
+                        }
+                    }
+        }
+    } while (changed);
+    return rounds;
+}
+
+/* Scatter of one shifted coarse grid's dense local box back to fine indexing. */
+static void grid_scatter_d(const geom_t *G, const long *o, const long *m, const double *src, double *dst)
+{
+    long x, y, z;
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) dst[grid_fine(G, o, x, y, z)] = src[lidx(m, x, y, z)];
+}
+
+/* Step 1 on one shifted grid: FSM with Alg. 1 (spacing H), Gamma fixed at g.
+ * Writes U and W on the grid's nodes. */
+static long step1_grid(const geom_t *G, const long *o, double H, const double *r, const unsigned char *gamma,
+                       const double *g, double *U, signed char *W, long max_sweeps, long *caps)
+{
+    long m[3], M, i, s, x, y, z;
+    double *ul, *rl;
+    unsigned char *fl;
+    signed char *wl;
+    int conv;
+    grid_box(G, o, m);
+    M = m[0] * m[1] * m[2];
+    ul = malloc(sizeof(double) * (size_t)M);
+    rl = malloc(sizeof(double) * (size_t)M);
+    fl = malloc((size_t)M);
+    wl = calloc((size_t)(3 * M), 1);
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long f = grid_fine(G, o, x, y, z), l = lidx(m, x, y, z);
+                rl[l] = r[f];
+                fl[l] = gamma[f] ? 1 : 0;
+                ul[l] = gamma[f] ? g[f] : INF; /* Sec. 1.1 initialisation */
+            }
+    s = fsm_local(G->d, m, H, rl, fl, ul, max_sweeps, &conv);
+    if (!conv) ++*caps;
+    winds_local(G->d, m, H, rl, fl, ul, wl);
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long f = grid_fine(G, o, x, y, z), l = lidx(m, x, y, z);
+                U[f] = ul[l];
+                for (i = 0; i < 3; ++i) W[3 * f + i] = wl[3 * l + i];
+            }
+    free(ul);
+    free(rl);
+    free(fl);
+    free(wl);
+    return s;
+}
+
+/* Step 4 on one shifted grid: Alg. 5.  Uk = U^k (for C_H(nbrs U^k)), uk/wk the
+ * Alg. 4 output, Wk = W^k.  Writes the swept U; W is set to w^k by the caller. */
+static long step4_grid(const geom_t *G, const long *o, double H, double theta, const double *r,
+                       const unsigned char *gamma, const double *g, const double *Uk, const double *uk,
+                       const signed char *wk, const signed char *Wk, double *U, long max_sweeps, long *caps)
+{
+    long m[3], M, s = 0, x, y, z;
+    int nq = 1 << G->d, d = G->d;
+    double *Ul, *Ukl, *Cold, *ukl, *rl;
+    unsigned char *fl;
+    int *Al;
+    signed char *wkl, *Wkl;
+    grid_box(G, o, m);
+    M = m[0] * m[1] * m[2];
+    Ul = malloc(sizeof(double) * (size_t)M);
+    Ukl = malloc(sizeof(double) * (size_t)M);
+    Cold = malloc(sizeof(double) * (size_t)M);
+    ukl = malloc(sizeof(double) * (size_t)M);
+    rl = malloc(sizeof(double) * (size_t)M);
+    fl = malloc((size_t)M);
+    Al = malloc(sizeof(int) * (size_t)M);
+    wkl = malloc((size_t)(3 * M));
+    Wkl = malloc((size_t)(3 * M));
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long f = grid_fine(G, o, x, y, z), l = lidx(m, x, y, z), xf[3];
+                int k;
+                coords(G, f, xf);
+                rl[l] = r[f];
+                fl[l] = gamma[f] ? 1 : 0;
+                Ukl[l] = Uk[f];
+                ukl[l] = uk[f];
+                Al[l] = coarse_axes(G, xf);
+                for (k = 0; k < 3; ++k) {
+                    wkl[3 * l + k] = wk[3 * f + k];
+                    Wkl[3 * l + k] = Wk[3 * f + k];
+                }
+                /* "Initialize U as described in Sec. 1.1" */
+                Ul[l] = gamma[f] ? g[f] : INF;
+            }
+    /* C_H(nbrs^H(U^k)) at every node, from the previous iterate. */
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long l = lidx(m, x, y, z);
+                double vm[3], vp[3];
+                signed char w[3];
+                nbrs(d, m, Ukl, x, y, z, vm, vp);
+                Cold[l] = orc_local_solve(d, vm, vp, rl[l] * H, w);
+            }
+    for (;;) {
+        int changed = 0, sg[3];
+        if (s >= max_sweeps) {
+            ++*caps;
+            break;
+        }
+        ordering(d, (int)(s % nq), sg);
+        for (x = start_of(m[0], sg[0]); x >= 0 && x < m[0]; x += sg[0])
+            for (y = start_of(m[1], sg[1]); y >= 0 && y < m[1]; y += sg[1])
+                for (z = start_of(m[2], sg[2]); z >= 0 && z < m[2]; z += sg[2]) {
+                    long l = lidx(m, x, y, z);
+                    double vm[3], vp[3], Ut, Unew;
+                    signed char Wt[3];
+                    int pass, k;
+                    if (fl[l]) continue;
+                    nbrs(d, m, Ul, x, y, z, vm, vp);
+                    Ut = orc_local_solve(d, vm, vp, rl[l] * H, Wt);
+                    /* Alg. 5 agreement test, per coarse-line axis: the fine wind
+                     * w^k, the coarse wind W^k and the current wind W~ all point
+                     * the same way (or are zero) along that axis. */
+                    pass = (Ut < INF) && (Cold[l] < INF);
+                    for (k = 0; k < d && pass; ++k) {
+                        int a = wkl[3 * l + k], b = Wkl[3 * l + k], c = Wt[k];
+                        if (!(Al[l] & (1 << k))) continue;
+                        if (!((a <= 0 && b <= 0 && c <= 0) || (a >= 0 && b >= 0 && c >= 0))) pass = 0;
+                    }
+                    if (pass)
+                        Unew = ukl[l] + theta * (Ut - Cold[l]);
+                    else
+                        Unew = ukl[l];
+                    if (!(Unew == Ul[l])) changed = 1;
+                    Ul[l] = Unew;
+                }
+        ++s;
+        if (!changed) break;
+    }
+    grid_scatter_d(G, o, m, Ul, U);
+    free(Ul);
+    free(Ukl);
+    free(Cold);
+    free(ukl);
+    free(rl);
+    free(fl);
+    free(Al);
+    free(wkl);
+    free(Wkl);
+    return s;
+}
+
+/* Step 2 + Step 3 on one subdomain: boundary data from (U, W), FSM, winds.
+ * ut/wt: the subdomain's local arrays ((S+1)^d nodes). */
+static long step23_tile(const geom_t *G, const int *t, double h, const double *r, const unsigned char *gamma,
+                        const double *g, const double *U, const signed char *W, double *ut, signed char *wt,
+                        long max_sweeps, long *caps)
+{
+    long m[3], M, x, y, z, s;
+    double *rl;
+    unsigned char *fl;
+    int conv, k;
+    for (k = 0; k < 3; ++k) m[k] = (k < G->d) ? G->S[k] + 1 : 1;
+    M = m[0] * m[1] * m[2];
+    rl = malloc(sizeof(double) * (size_t)M);
+    fl = malloc((size_t)M);
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long lc[3] = {x, y, z}, xf[3], f, l = lidx(m, x, y, z);
+                int inflow = 0, face = 0;
+                for (k = 0; k < 3; ++k) xf[k] = (k < G->d) ? t[k] * G->S[k] + lc[k] : 0;
+                f = xf[0] + G->n[0] * (xf[1] + G->n[1] * xf[2]);
+                rl[l] = r[f];
+                for (k = 0; k < 3; ++k) wt[3 * l + k] = 0;
+                if (gamma[f]) {
+                    fl[l] = 1;
+                    ut[l] = g[f];
+                    continue;
+                }
+                /* Step 2: inflow when W . n > 0 for an inward normal n. */
+                for (k = 0; k < G->d; ++k) {
+                    if (lc[k] == 0) {
+                        face = 1;
+                        if (W[3 * f + k] > 0) inflow = 1;
+                    }
+                    if (lc[k] == m[k] - 1) {
+                        face = 1;
+                        if (W[3 * f + k] < 0) inflow = 1;
+                    }
+                }
+                if (face && inflow) {
+                    fl[l] = 1;
+                    ut[l] = U[f];
+                    for (k = 0; k < 3; ++k) wt[3 * l + k] = W[3 * f + k];
+                } else {
+                    fl[l] = 0;
+                    ut[l] = INF;
+                }
+            }
+    s = fsm_local(G->d, m, h, rl, fl, ut, max_sweeps, &conv);
+    if (!conv) ++*caps;
+    winds_local(G->d, m, h, rl, fl, ut, wt);
+    free(rl);
+    free(fl);
+    return s;
+}
+
+/* Alg. 4 at every coarse-set node: choose u^k, w^k among the subdomain copies. */
+static void alg4(const geom_t *G, double **tu, signed char **tw, const signed char *W, double *uk, signed char *wk)
+{
+    long i;
+    long tm[3];
+    int k;
+    for (k = 0; k < 3; ++k) tm[k] = (k < G->d) ? G->S[k] + 1 : 1;
+    for (i = 0; i < G->N; ++i) {
+        long x[3];
+        long cand[3][2];
+        int nc[3], B = 0;
+        int A, q, ncopies, best, sel[3], ok;
+        long cidx[8], lidxs[8];
+        coords(G, i, x);
+        A = coarse_axes(G, x);
+        if (!A) continue;
+        for (k = 0; k < 3; ++k) {
+            if (k >= G->d) {
+                cand[k][0] = 0;
+                nc[k] = 1;
+                continue;
+            }
+            if (x[k] % G->S[k] == 0 && x[k] > 0 && x[k] < G->n[k] - 1) {
+                cand[k][0] = x[k] / G->S[k] - 1; /* minus side */
+                cand[k][1] = x[k] / G->S[k];     /* plus side */
+                nc[k] = 2;
+                B |= 1 << k;
+            } else {
+                long tt = x[k] / G->S[k];
+                if (tt >= G->T[k]) tt = G->T[k] - 1;
+                cand[k][0] = tt;
+                nc[k] = 1;
+            }
+        }
+        /* copies in ascending linear subdomain index (axis 0 fastest) */
+        ncopies = 0;
+        {
+            int a0, a1, a2;
+            for (a2 = 0; a2 < nc[2]; ++a2)
+                for (a1 = 0; a1 < nc[1]; ++a1)
+                    for (a0 = 0; a0 < nc[0]; ++a0) {
+                        long tt[3] = {cand[0][a0], cand[1][a1], cand[2][a2]};
+                        long lc[3];
+                        for (k = 0; k < 3; ++k) lc[k] = (k < G->d) ? x[k] - tt[k] * G->S[k] : 0;
+                        cidx[ncopies] = tt[0] + G->T[0] * (tt[1] + G->T[1] * tt[2]);
+                        lidxs[ncopies] = lidx(tm, lc[0], lc[1], lc[2]);
+                        ++ncopies;
+                    }
+        }
+        best = 0;
+        ok = 1;
+        for (k = 0; k < 3; ++k) sel[k] = 0;
+        if (B) {
+            for (k = 0; k < G->d && ok; ++k) {
+                int allneg = 1, allpos = 1;
+                if (!(B & (1 << k))) continue;
+                if (W[3 * i + k] > 0) allneg = 0;
+                if (W[3 * i + k] < 0) allpos = 0;
+                for (q = 0; q < ncopies; ++q) {
+                    int wv = tw[cidx[q]][3 * lidxs[q] + k];
+                    if (wv > 0) allneg = 0;
+                    if (wv < 0) allpos = 0;
+                }
+                /* Alg. 4: first branch (wind toward -axis: take the plus-side
+                 * copy) wins when both hold; then the minus-side copy. */
+                if (allneg)
+                    sel[k] = 1;
+                else if (allpos)
+                    sel[k] = 0;
+                else
+                    ok = 0;
+            }
+            if (ok) {
+                /* index of the selected copy in the enumeration */
+                int stride = 1;
+                best = 0;
+                for (k = 0; k < 3; ++k) {
+                    best += sel[k] * stride;
+                    stride *= nc[k];
+                }
+            } else {
+                /* otherwise the minimum; ties keep the lowest subdomain index */
+                best = 0;
+                for (q = 1; q < ncopies; ++q)
+                    if (tu[cidx[q]][lidxs[q]] < tu[cidx[best]][lidxs[best]]) best = q;
+            }
+        }
+        uk[i] = tu[cidx[best]][lidxs[best]];
+        for (k = 0; k < 3; ++k) wk[3 * i + k] = tw[cidx[best]][3 * lidxs[best] + k];
+    }
+}
+
+static double coarse_delta(const geom_t *G, const double *U1, const double *U0)
+{
+    long i;
+    double dmax = 0.0;
+    for (i = 0; i < G->N; ++i) {
+        long x[3];
+        double dv;
+        coords(G, i, x);
+        if (!coarse_axes(G, x)) continue;
+        if (U1[i] == U0[i]) continue; /* covers inf == inf */
+        dv = fabs(U1[i] - U0[i]);
+        if (dv > dmax) dmax = dv;
+    }
+    return dmax;
+}
+
+int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
+           double *u_out, double *U_out, double *delta_log, orc_dd_stats *st)
+{
+    geom_t G;
+    long i, ntiles;
+    int k, it;
+    double H, delta = INF;
+    double *U, *Uprev, *uk, **tu;
+    signed char *W, *wk, **tw;
+    long tilenodes;
+    orc_dd_stats S0;
+    memset(&S0, 0, sizeof(S0));
+    if (p->d < 2 || p->d > 3 || p->c < 1) return -1;
+    memset(&G, 0, sizeof(G));
+    G.d = p->d;
+    G.c = p->c;
+    for (k = 0; k < 3; ++k) {
+        G.n[k] = (k < p->d) ? p->n[k] : 1;
+        G.T[k] = (k < p->d) ? p->tiles[k] : 1;
+        if (k < p->d) {
+            if (G.T[k] < 1 || (G.n[k] - 1) % G.T[k]) return -1;
+            G.S[k] = (G.n[k] - 1) / G.T[k];
+            if (G.S[k] % G.c) return -1;
+        } else
+            G.S[k] = 0;
+    }
+    G.N = G.n[0] * G.n[1] * G.n[2];
+    G.st[0] = 1;
+    G.st[1] = G.n[0];
+    G.st[2] = G.n[0] * G.n[1];
+    H = G.c * p->h;
+    ntiles = (long)G.T[0] * G.T[1] * G.T[2];
+    tilenodes = 1;
+    for (k = 0; k < p->d; ++k) tilenodes *= G.S[k] + 1;
+
+    U = malloc(sizeof(double) * (size_t)G.N);
+    Uprev = malloc(sizeof(double) * (size_t)G.N);
+    uk = malloc(sizeof(double) * (size_t)G.N);
+    W = calloc((size_t)(3 * G.N), 1);
+    wk = calloc((size_t)(3 * G.N), 1);
+    tu = malloc(sizeof(double *) * (size_t)ntiles);
+    tw = malloc(sizeof(signed char *) * (size_t)ntiles);
+    for (i = 0; i < ntiles; ++i) {
+        tu[i] = malloc(sizeof(double) * (size_t)tilenodes);
+        tw[i] = malloc((size_t)(3 * tilenodes));
+    }
+    for (i = 0; i < G.N; ++i) U[i] = uk[i] = NAN;
+
+    /* Step 1: every shifted coarse grid, independently; then the causal sweep. */
+    {
+        long o[3];
+        int first = 1;
+        while (next_offset(&G, o, first)) {
+            long s;
+            first = 0;
+            s = step1_grid(&G, o, H, r, gamma, g, U, W, p->max_coarse_sweeps, &S0.coarse_cap_hits);
+            if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
+        }
+    }
+    {
+        long cr = causal_sweep(&G, U, W);
+        if (cr > S0.causal_rounds_max) S0.causal_rounds_max = cr;
+    }
+    if (delta_log)
+        for (k = 0; k <= p->max_iter; ++k) delta_log[k] = NAN;
+    if (delta_log) delta_log[0] = INF;
+
+    for (it = 0;; ++it) {
+        /* Steps 2 + 3: every subdomain independently. */
+        int t[3];
+        long ti = 0;
+        for (t[2] = 0; t[2] < G.T[2]; ++t[2])
+            for (t[1] = 0; t[1] < G.T[1]; ++t[1])
+                for (t[0] = 0; t[0] < G.T[0]; ++t[0]) {
+                    long s = step23_tile(&G, t, p->h, r, gamma, g, U, W, tu[ti], tw[ti], p->max_fsm_sweeps,
+                                         &S0.fsm_cap_hits);
+                    if (s > S0.fsm_sweeps_max) S0.fsm_sweeps_max = s;
+                    ++ti;
+                }
+        /* Alg. 4 */
+        alg4(&G, tu, tw, W, uk, wk);
+        S0.iters = it;
+        if (it == p->max_iter) break;
+        if (it >= 1 && delta < p->tol) {
+            S0.converged = 1;
+            break;
+        }
+        /* Step 4: Alg. 5 on every shifted grid, W = w^k, then the causal sweep. */
+        memcpy(Uprev, U, sizeof(double) * (size_t)G.N);
+        {
+            long o[3];
+            int first = 1;
+            double *Unew = malloc(sizeof(double) * (size_t)G.N);
+            memcpy(Unew, U, sizeof(double) * (size_t)G.N);
+            while (next_offset(&G, o, first)) {
+                long s;
+                first = 0;
+                s = step4_grid(&G, o, H, p->theta, r, gamma, g, Uprev, uk, wk, W, Unew, p->max_coarse_sweeps,
+                               &S0.coarse_cap_hits);
+                if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
+            }
+            memcpy(U, Unew, sizeof(double) * (size_t)G.N);
+            free(Unew);
+        }
+        for (i = 0; i < G.N; ++i) {
+            long x[3];
+            coords(&G, i, x);
+            if (coarse_axes(&G, x)) {
+                int kk;
+                for (kk = 0; kk < 3; ++kk) W[3 * i + kk] = wk[3 * i + kk];
+            }
+        }
+        {
+            long cr = causal_sweep(&G, U, W);
+            if (cr > S0.causal_rounds_max) S0.causal_rounds_max = cr;
+        }
+        delta = coarse_delta(&G, U, Uprev);
+        if (delta_log && it + 1 <= p->max_iter) delta_log[it + 1] = delta;
+    }
+    S0.last_delta = delta;
+
+    /* Patched fine solution: coarse-set nodes take u^k, the rest their
+     * (unique) subdomain's value. */
+    for (i = 0; i < G.N; ++i) {
+        long x[3], tt[3], lc[3], tl;
+        long tm[3];
+        coords(&G, i, x);
+        if (coarse_axes(&G, x)) {
+            u_out[i] = uk[i];
+            continue;
+        }
+        for (k = 0; k < 3; ++k) {
+            tm[k] = (k < G.d) ? G.S[k] + 1 : 1;
+            tt[k] = (k < G.d) ? x[k] / G.S[k] : 0;
+            lc[k] = (k < G.d) ? x[k] - tt[k] * G.S[k] : 0;
+        }
+        tl = tt[0] + G.T[0] * (tt[1] + G.T[1] * tt[2]);
+        u_out[i] = tu[tl][lidx(tm, lc[0], lc[1], lc[2])];
+    }
+    if (U_out)
+        for (i = 0; i < G.N; ++i) U_out[i] = U[i];
+    if (st) *st = S0;
+
+    for (i = 0; i < ntiles; ++i) {
+        free(tu[i]);
+        free(tw[i]);
+    }
+    free(tu);
+    free(tw);
+    free(U);
+    free(Uprev);
+    free(uk);
+    free(W);
+    free(wk);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of the converged discrete system (a project addition; the paper has */
+/* no gradient).  At a converged u every reached non-Gamma node satisfies       */
+/* u_i = F(a_i, r_i) with a_i the per-axis neighbour minima of the branch the   */
+/* local solve takes.  Linearising: du_i = sum_j dF/da_j du_j + dF/dr_i dr_i,   */
+/* where j runs over the neighbours used, all with smaller u (causality).  For  */
+/* a scalar J(u), lambda = dJ/du + sum over downwind k of lambda_k dF_k/du_i,   */
+/* solved by visiting nodes in decreasing u; dJ/dr_i = lambda_i dF_i/dr_i.      */
+/* Branch derivatives: one term dF/da = 1, dF/dr = h; several terms with        */
+/* sum_j (u - a_j)^2 = (r h)^2: dF/da_j = (u-a_j)/D, dF/dr = r h^2 / D,         */
+/* D = sum_j (u - a_j).                                                         */
+/* ------------------------------------------------------------------------- */
+static int cmp_desc(const void *A, const void *B)
+{
+    const hent *a = A, *b = B;
+    if (a->v > b->v) return -1;
+    if (a->v < b->v) return 1;
+    return (a->i < b->i) ? -1 : (a->i > b->i);
+}
+
+void orc_adjoint(int d, const long *n, double h, const double *r, const unsigned char *gamma,
+                 const double *u, const double *dJdu, double *dJdr)
+{
+    long m[3] = {n[0], d > 1 ? n[1] : 1, d > 2 ? n[2] : 1};
+    long N = m[0] * m[1] * m[2], i, cnt = 0;
+    long st[3] = {1, m[0], m[0] * m[1]};
+    hent *ord = malloc(sizeof(hent) * (size_t)N);
+    double *lam = malloc(sizeof(double) * (size_t)N);
+    for (i = 0; i < N; ++i) {
+        lam[i] = dJdu[i];
+        dJdr[i] = 0.0;
+        if (!gamma[i] && u[i] < INF) {
+            ord[cnt].v = u[i];
+            ord[cnt].i = i;
+            ++cnt;
+        }
+    }
+    qsort(ord, (size_t)cnt, sizeof(hent), cmp_desc);
+    for (i = 0; i < cnt; ++i) {
+        long j = ord[i].i, c[3];
+        double vm[3], vp[3], ut, D = 0.0;
+        signed char w[3];
+        long nb[3];
+        int k, used = 0;
+        c[0] = j % m[0];
+        c[1] = (j / m[0]) % m[1];
+        c[2] = j / (m[0] * m[1]);
+        nbrs(d, m, u, c[0], c[1], c[2], vm, vp);
+        ut = orc_local_solve(d, vm, vp, r[j] * h, w);
+        (void)ut;
+        for (k = 0; k < d; ++k) {
+            nb[k] = -1;
+            if (w[k] > 0) nb[k] = j - st[k]; /* upwind on the minus side */
+            if (w[k] < 0) nb[k] = j + st[k];
+            if (nb[k] >= 0) {
+                D += u[j] - u[nb[k]];
+                ++used;
+            }
+        }
+        if (used == 0) continue;
+        if (used == 1) {
+            for (k = 0; k < d; ++k)
+                if (nb[k] >= 0) lam[nb[k]] += lam[j];
+            dJdr[j] = lam[j] * h;
+        } else {
+            if (!(D > 0.0)) continue;
+            for (k = 0; k < d; ++k)
+                if (nb[k] >= 0) lam[nb[k]] += lam[j] * (u[j] - u[nb[k]]) / D;
+            dJdr[j] = lam[j] * r[j] * h * h / D;
+        }
+    }
+    free(ord);
+    free(lam);
+}

@@ -1,0 +1,89 @@
+/*
+ * eik_oracle.h -- serial FP64 CPU oracle for the two-scale domain-decomposition
+ * Eikonal solver of Martin & Tsai, "A Multiscale Domain Decomposition Algorithm
+ * for Boundary Value Problems for Eikonal Equations" (arXiv:1805.04198).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the plain, slow, obviously-correct
+ * statement of what the method computes.  Only the test suite, the smoke check
+ * and the CPU-baseline leg of bench.py load it.  It shares no code with the CUDA
+ * path (no headers, no helpers, no constants) and must never be called by it.
+ *
+ * Layout: nodes indexed [z][y][x], axis 0 (x) fastest, n[a] nodes per axis
+ * (unused axes have n[a] = 1).  All arrays are caller-owned, FP64.
+ * A wind is stored as d signed bytes per node (component a at [3*node + a]),
+ * each in {-1, 0, +1}, +1 meaning travel toward +axis (upwind neighbour on the
+ * minus side).
+ */
+#ifndef EIK_ORACLE_H
+#define EIK_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Godunov local solve, Sec. 1.1 eq. (godonuv) with Alg. 3's per-axis choice.
+ * vm[a], vp[a]: neighbour values on the minus / plus side of axis a
+ * (+inf where the neighbour does not exist: the one-sided rule of Sec. 1.1).
+ * Returns u~; writes the wind of the branch taken into w[0..d-1]. */
+double orc_local_solve(int d, const double *vm, const double *vp, double rh, signed char *w);
+
+/* Plain fast sweeping method (Sec. 1.1) over a whole grid.
+ * gamma[i] != 0 marks Gamma (u fixed at g[i]); every other node starts at +inf.
+ * Sweeps cycle through the 2^d orderings of Sec. 1.1 until one sweep changes no
+ * value or max_sweeps sweeps ran.  w (nullable) receives the wind of the local
+ * solve at the final state.  Returns the number of sweeps; *converged set to 1
+ * if the last sweep changed nothing. */
+long orc_fsm(int d, const long *n, double h, const double *r, const unsigned char *gamma,
+             const double *g, double *u, signed char *w, long max_sweeps, int *converged);
+
+/* Dijkstra / fast-marching solve of the same discrete system (Sec. 1.1: the
+ * scheme is causal, so accepting nodes in increasing order of value gives its
+ * solution).  Used only to cross-check orc_fsm. */
+void orc_fmm(int d, const long *n, double h, const double *r, const unsigned char *gamma,
+             const double *g, double *u);
+
+typedef struct {
+    int d;
+    long n[3];            /* nodes per axis */
+    double h;             /* fine spacing */
+    int tiles[3];         /* subdomains per axis, (n[a]-1) % tiles[a] == 0 */
+    int c;                /* coarse ratio, H = c h; (n[a]-1)/tiles[a] % c == 0 */
+    double theta;         /* weight of the theta-parareal correction (Sec. 2, Alg. 5) */
+    int max_iter;         /* parareal iteration cap */
+    double tol;           /* stop when max |U^k - U^{k-1}| < tol (k >= 1) */
+    long max_fsm_sweeps;  /* per fine subdomain solve */
+    long max_coarse_sweeps; /* per coarse grid solve (Step 1 and Step 4) */
+} orc_dd_params;
+
+typedef struct {
+    int iters;            /* k of the last fine solve (number of coarse updates done) */
+    int converged;        /* 1 if stopped by tol */
+    double last_delta;    /* max |U^k - U^{k-1}| of the last update (inf if none) */
+    long fsm_sweeps_max;  /* largest sweep count of any fine subdomain solve */
+    long coarse_sweeps_max; /* largest sweep count of any coarse grid solve */
+    long fsm_cap_hits;    /* fine solves stopped by max_fsm_sweeps */
+    long coarse_cap_hits; /* coarse solves stopped by max_coarse_sweeps */
+    long causal_rounds_max; /* rounds of 2^d causal passes until no change (>=1) */
+} orc_dd_stats;
+
+/* The two-scale DD / theta-parareal iteration of Sec. 3 (Steps 1-4, Alg. 1-5),
+ * d = 2 or 3.  Outputs:
+ *   u_out     fine solution patched from the last subdomain solves (coarse-set
+ *             nodes take the Alg. 4 value);
+ *   U_out     (nullable) coarse values U^k of the last iterate, +inf... only
+ *             meaningful on the coarse set, NaN elsewhere;
+ *   delta_log (nullable) max_iter+1 entries: delta_log[k] = max|U^k - U^{k-1}|
+ *             (delta_log[0] = inf).
+ * Returns 0 on success, -1 on invalid parameters. */
+int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
+           double *u_out, double *U_out, double *delta_log, orc_dd_stats *st);
+
+/* Discrete adjoint of the converged Godunov system at u (see oracle source):
+ * given dJ/du at every node, returns dJ/dr at every node (0 on Gamma and on
+ * unreached nodes). */
+void orc_adjoint(int d, const long *n, double h, const double *r, const unsigned char *gamma,
+                 const double *u, const double *dJdu, double *dJdr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

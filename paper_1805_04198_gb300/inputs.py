@@ -1,0 +1,143 @@
+"""Seeded synthetic inputs for the two-scale DD Eikonal solver.
+
+This module holds no arithmetic of the method: it only draws slowness fields
+r_eps, source sets Gamma and boundary values g.  Both the CUDA path and the CPU
+oracle are fed from here (fields are generated in FP64 and rounded to the run
+dtype by the caller; the oracle receives the same rounded values promoted back
+to FP64).
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), top 53 bits -> [0, 1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_MASK = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 generator (Steele, Lea & Flood 2014)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+    def randint(self, lo: int, hi: int) -> int:
+        """Uniform integer in [lo, hi] (inclusive)."""
+        return lo + int(self.uniform() * (hi - lo + 1))
+
+
+def node_coords(shape, h):
+    """Per-axis node coordinates (x, y[, z]) as 1-D arrays; shape is (.., y, x)."""
+    return [np.arange(n, dtype=np.float64) * h for n in reversed(shape)]
+
+
+def sin_product(shape, h, amp, eps):
+    """r = 1 + amp * prod_a sin(2 pi x_a / eps) (the paper's smooth oscillatory r)."""
+    cs = node_coords(shape, h)
+    d = len(shape)
+    f = np.ones(shape, dtype=np.float64)
+    for a, c in enumerate(cs):
+        s = np.sin(2.0 * math.pi * c / eps)
+        view = [1] * d
+        view[d - 1 - a] = -1
+        f = f * s.reshape(view)
+    return 1.0 + amp * f
+
+
+def fourier_modes(seed, nmodes, kmin, kmax):
+    """Wave vectors (|k| ~ U[kmin, kmax], angle ~ U[0, 2pi)) and phases of a 2-D field."""
+    rng = SplitMix64(seed)
+    modes = []
+    for _ in range(nmodes):
+        kmag = kmin + (kmax - kmin) * rng.uniform()
+        ang = 2.0 * math.pi * rng.uniform()
+        phi = 2.0 * math.pi * rng.uniform()
+        modes.append((kmag * math.cos(ang), kmag * math.sin(ang), phi))
+    return modes
+
+
+def fourier_field(shape, h, seed, eps, nmodes=32):
+    """F = sum_q cos(2 pi k_q . x + phi_q) with |k_q| in [1/eps, 2/eps], 2-D only."""
+    ny, nx = shape
+    x = np.arange(nx, dtype=np.float64) * h
+    y = np.arange(ny, dtype=np.float64) * h
+    F = np.zeros(shape, dtype=np.float64)
+    for kx, ky, phi in fourier_modes(seed, nmodes, 1.0 / eps, 2.0 / eps):
+        ex = np.exp(1j * (2.0 * math.pi * kx * x))
+        ey = np.exp(1j * (2.0 * math.pi * ky * y + phi))
+        F += np.real(ey[:, None] * ex[None, :])
+    return F
+
+
+def multiscale_r(shape, h, seed, eps, r0_slope=0.3, amp=0.4, floor=0.2):
+    """r = clip(1 + r0_slope x + amp F / max|F|, floor): smooth r0 plus a_eps."""
+    F = fourier_field(shape, h, seed, eps)
+    x = np.arange(shape[1], dtype=np.float64) * h
+    r = 1.0 + r0_slope * x[None, :] + amp * F / np.max(np.abs(F))
+    return np.maximum(r, floor)
+
+
+def point_source(shape, idx):
+    """Gamma = one node (index tuple in array order), g = 0."""
+    gamma = np.zeros(shape, dtype=np.uint8)
+    gamma[idx] = 1
+    return gamma, np.zeros(shape, dtype=np.float64)
+
+
+def left_edge_source(shape):
+    """Gamma = every node with x = 0, g = 0."""
+    gamma = np.zeros(shape, dtype=np.uint8)
+    gamma[..., 0] = 1
+    return gamma, np.zeros(shape, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Named workloads (sizes follow the benchmark configurations).
+# --------------------------------------------------------------------------
+SEED_C1 = 1805041981
+SEED_C3 = 1805041982
+SEED_C4 = 1805041983
+
+
+def workload_c0():
+    """2-D 257^2, h=1/256, r = 1 + .5 sin(2 pi x/eps) sin(2 pi y/eps), eps = 1/16,
+    point source at (0.5, 0.5), 4x4 subdomains, coarse ratio 8 (33^2), theta 1."""
+    n = 257
+    h = 1.0 / 256
+    r = sin_product((n, n), h, 0.5, 1.0 / 16)
+    gamma, g = point_source((n, n), (128, 128))
+    return dict(name="c0_2d_257_pointsrc", r=r, gamma=gamma, g=g, h=h, tiles=(4, 4), c=8, theta=1.0,
+                max_iter=10, tol=1e-10)
+
+
+def workload_c1(n=4097, tiles=16, c=16):
+    """2-D 4097^2, h=1/4096, r = clip(1 + .3x + .4 F/max|F|, .2), 32 Fourier modes,
+    eps = 1/64, Gamma = left edge, 16x16 subdomains, coarse 257^2 (c = 16)."""
+    h = 1.0 / (n - 1)
+    r = multiscale_r((n, n), h, SEED_C1, 1.0 / 64)
+    gamma, g = left_edge_source((n, n))
+    return dict(name="c1_2d_%d_leftedge" % n, r=r, gamma=gamma, g=g, h=h, tiles=(tiles, tiles), c=c,
+                theta=1.0, max_iter=2 * tiles + 10, tol=0.0)
+
+
+def workload_c2(n=257, tiles=8, c=8):
+    """3-D 257^3, h=1/256, r = 1 + .4 sin sin sin (eps = 1/32), centre source."""
+    h = 1.0 / (n - 1)
+    r = sin_product((n, n, n), h, 0.4, 1.0 / 32)
+    m = (n - 1) // 2
+    gamma, g = point_source((n, n, n), (m, m, m))
+    return dict(name="c2_3d_%d_pointsrc" % n, r=r, gamma=gamma, g=g, h=h, tiles=(tiles, tiles, tiles), c=c,
+                theta=1.0, max_iter=2 * tiles + 10, tol=0.0)

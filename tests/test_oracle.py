@@ -1,0 +1,272 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks a hand-derived value,
+an independent algorithm (Dijkstra), an exact solution, a theorem of the paper,
+or an invariant of the discrete scheme.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+INF = math.inf
+
+
+def _val(tok):
+    return float(eval(tok, {"sqrt": math.sqrt, "inf": INF}))
+
+
+def test_local_solve_2d_hand_values():
+    """Sec. 3.2 closed form of C_H / Alg. 3 (with direction-of-travel winds)."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "local_solve_2d.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) >= 8
+    for vmx, vpx, vmy, vpy, rh, u, wx, wy in rows:
+        got, w = O.local_solve([_val(vmx), _val(vmy)], [_val(vpx), _val(vpy)], _val(rh))
+        want = _val(u)
+        if math.isinf(want):
+            assert math.isinf(got)
+        else:
+            assert got == pytest.approx(want, rel=1e-15, abs=1e-15)
+            assert w == (int(wx), int(wy))
+
+
+def test_local_solve_quadratic_residual():
+    """The two- and three-term branches solve sum_j (u - a_j)^2 = (r h)^2."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        a = rng.uniform(0, 1, 3)
+        rh = rng.uniform(0.05, 1.0)
+        u2, w2 = O.local_solve([a[0], a[1]], [INF, INF], rh)
+        if abs(a[0] - a[1]) < rh:
+            assert (u2 - a[0]) ** 2 + (u2 - a[1]) ** 2 == pytest.approx(rh * rh, rel=1e-12)
+            assert u2 > max(a[0], a[1])
+        else:
+            assert u2 == min(a[0], a[1]) + rh
+        u3, w3 = O.local_solve(list(a), [INF] * 3, rh)
+        if all(w3):
+            assert sum((u3 - ai) ** 2 for ai in a) == pytest.approx(rh * rh, rel=1e-10)
+            assert u3 > max(a)
+        # causality: the solve never goes below its inputs plus nothing
+        assert u3 > min(a)
+        # 3-D with one axis missing reduces exactly to the 2-D solve
+        u32, w32 = O.local_solve([a[0], a[1], INF], [INF] * 3, rh)
+        assert u32 == u2 and w32[:2] == w2 and w32[2] == 0
+
+
+def test_local_solve_3d_symmetric():
+    """Equal minima on three axes: 3 (u - a)^2 = (rh)^2 -> u = a + rh/sqrt(3)."""
+    u, w = O.local_solve([0.25, 0.25, 0.25], [INF, INF, INF], 0.3)
+    assert u == pytest.approx(0.25 + 0.3 / math.sqrt(3), rel=1e-15)
+    assert w == (1, 1, 1)
+    u1, w1 = O.local_solve([0.5], [INF], 0.125)
+    assert u1 == 0.625 and w1 == (1,)
+
+
+@pytest.mark.parametrize("shape", [(17, 17), (33, 21), (9, 9, 9), (12, 7, 10)])
+def test_fsm_equals_dijkstra(shape):
+    """Sec. 1.1: the scheme is causal, so the FSM fixed point is the Dijkstra
+    (fast marching) solution of the same discrete equations -- bitwise."""
+    rng = np.random.default_rng(sum(shape))
+    r = rng.uniform(0.5, 2.0, shape)
+    gamma = (rng.uniform(size=shape) < 0.02).astype(np.uint8)
+    gamma.flat[len(gamma.flat) // 3] = 1
+    g = rng.uniform(0.0, 0.1, shape)
+    u, sweeps, conv = O.fsm(r, gamma, g, 0.1)
+    v = O.fmm(r, gamma, g, 0.1)
+    assert conv
+    assert np.array_equal(u, v)
+
+
+def test_fsm_linear_data_exact():
+    """r = 1, Gamma = {x = 0}, g = 0: u = x exactly (|a-b| = h is not < h, so
+    every update is the one-term branch); h a power of two keeps it exact."""
+    n = 65
+    h = 1.0 / 64
+    gamma = np.zeros((n, n), np.uint8)
+    gamma[:, 0] = 1
+    u, s, c = O.fsm(np.ones((n, n)), gamma, 0.0, h)
+    x = np.arange(n) * h
+    assert np.array_equal(u, np.broadcast_to(x[None, :], (n, n)))
+    # 2^d sweeps suffice when characteristics do not turn (Sec. 1.1): one
+    # ordering sweeps it, the next confirms nothing changes.
+    assert c and s <= 4
+    # constant r on a 3-D box with g = r * z on the face z = 0 ... linear in z
+    gamma3 = np.zeros((9, 9, 9), np.uint8)
+    gamma3[0] = 1
+    u3, _, _ = O.fsm(np.full((9, 9, 9), 2.0), gamma3, 0.0, 0.25)
+    z = np.arange(9) * 0.25 * 2.0
+    assert np.array_equal(u3, np.broadcast_to(z[:, None, None], u3.shape))
+
+
+def test_fsm_point_source_first_order():
+    """r = 1, point source: u -> |x - x0| with observed order close to one
+    (first-order scheme, log factor at the source)."""
+    errs = []
+    for n in (65, 129, 257, 513):
+        h = 1.0 / (n - 1)
+        m = n // 2
+        gamma = np.zeros((n, n), np.uint8)
+        gamma[m, m] = 1
+        u, _, _ = O.fsm(np.ones((n, n)), gamma, 0.0, h)
+        x = np.arange(n) * h
+        ex = np.sqrt((x[None, :] - 0.5) ** 2 + (x[:, None] - 0.5) ** 2)
+        assert np.all(u >= ex - 1e-12)  # the Godunov scheme overestimates distance
+        errs.append(np.max(np.abs(u - ex)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(orders) > 0.7 and max(orders) < 1.1, orders
+
+
+def test_fsm_invariants():
+    """Monotone decrease across sweeps, u >= min g, comparison principle, and
+    the discrete equation holds at every non-Gamma node of the fixed point."""
+    rng = np.random.default_rng(7)
+    shape = (25, 31)
+    r1 = rng.uniform(0.5, 1.5, shape)
+    r2 = r1 + rng.uniform(0.0, 0.5, shape)
+    gamma = np.zeros(shape, np.uint8)
+    gamma[3, 4] = gamma[20, 27] = 1
+    g = np.full(shape, 0.2)
+    prev = np.full(shape, INF)
+    for k in range(1, 12):
+        u, _, _ = O.fsm(r1, gamma, g, 0.05, max_sweeps=k)
+        assert np.all(u <= prev)
+        prev = u
+    u1, _, _ = O.fsm(r1, gamma, g, 0.05)
+    u2, _, _ = O.fsm(r2, gamma, g, 0.05)
+    assert np.all(u1 >= 0.2) and np.all(u1 <= u2)
+    # residual: the local solve at the final neighbours reproduces u bitwise
+    ny, nx = shape
+    for j in range(ny):
+        for i in range(nx):
+            if gamma[j, i]:
+                continue
+            vm = [u1[j, i - 1] if i > 0 else INF, u1[j - 1, i] if j > 0 else INF]
+            vp = [u1[j, i + 1] if i < nx - 1 else INF, u1[j + 1, i] if j < ny - 1 else INF]
+            ut, _ = O.local_solve(vm, vp, r1[j, i] * 0.05)
+            assert ut == u1[j, i]
+
+
+def _model_problem(N, M):
+    """Sec. 4 model problem: strip [0,1] x [0,H], r = 1, Gamma = bottom and left
+    edges with g = sqrt(x^2 + y^2); subdomains of width H = 1/N, M cells each."""
+    h = 1.0 / (N * M)
+    nx, ny = N * M + 1, M + 1
+    x = np.arange(nx) * h
+    y = np.arange(ny) * h
+    r = np.ones((ny, nx))
+    gamma = np.zeros((ny, nx), np.uint8)
+    gamma[0, :] = 1
+    gamma[:, 0] = 1
+    g = np.sqrt(x[None, :] ** 2 + y[:, None] ** 2)
+    return r, gamma, g, h
+
+
+@pytest.mark.parametrize("theta", [0.1, 0.5, 1.0])
+def test_dd_theorem1_exactness(theta):
+    """Theorem 1 (Sec. 4.1): on the model problem U^k_{i,j} = u^f_{i,j} for
+    k >= i, for any theta -- bitwise, since both sides reach the same FP fixed
+    point of the same local solves."""
+    N, M = 8, 8
+    r, gamma, g, h = _model_problem(N, M)
+    uf, _, _ = O.fsm(r, gamma, g, h)
+    for k in range(N + 1):
+        u, st, log, U = O.dd(r, gamma, g, h, (N, 1), M, theta=theta, max_iter=k, tol=-1.0,
+                             return_coarse=True)
+        for i in range(N + 1):
+            col = i * M
+            same = np.array_equal(U[1:, col], uf[1:, col])
+            if i <= k:
+                assert same, (theta, k, i)
+        if k == N:
+            assert np.array_equal(u, uf)
+
+
+def test_dd_theta1_unstable_on_model_problem():
+    """Sec. 4: theta = 1 (plain parareal) has large, non-monotone errors on the
+    model problem before exactness catches up; a small theta decreases steadily."""
+    N, M = 10, 10
+    r, gamma, g, h = _model_problem(N, M)
+    uf, _, _ = O.fsm(r, gamma, g, h)
+    e1, e01 = [], []
+    for k in range(N):
+        _, _, _, U1 = O.dd(r, gamma, g, h, (N, 1), M, theta=1.0, max_iter=k, tol=-1, return_coarse=True)
+        _, _, _, U2 = O.dd(r, gamma, g, h, (N, 1), M, theta=0.1, max_iter=k, tol=-1, return_coarse=True)
+        e1.append(np.max(np.abs(U1[:, ::M] - uf[:, ::M])))
+        e01.append(np.max(np.abs(U2[:, ::M] - uf[:, ::M])))
+    assert max(e1) > 2 * e1[0]          # theta = 1 error grows
+    assert all(e01[i + 1] <= e01[i] * 1.0001 for i in range(len(e01) - 1))
+
+
+def test_dd_single_subdomain_is_fsm():
+    """One subdomain: every subdomain face is the domain boundary (never inflow),
+    so Step 3 is the plain FSM on the whole grid and DD returns u^f bitwise."""
+    rng = np.random.default_rng(3)
+    n = 33
+    r = rng.uniform(0.5, 2.0, (n, n))
+    gamma = np.zeros((n, n), np.uint8)
+    gamma[5, 9] = 1
+    uf, _, _ = O.fsm(r, gamma, 0.0, 1 / 32)
+    u, st, _ = O.dd(r, gamma, 0.0, 1 / 32, (1, 1), 8, theta=0.5, max_iter=2, tol=-1)
+    assert np.array_equal(u, uf)
+
+
+def test_dd_fixed_point_is_fine_solution():
+    """A converged DD iterate reproduces the global fine FSM solution u^f
+    (Sec. 5 reports errors against u^f): smooth r, point source, theta 0.2."""
+    n = 129
+    h = 1.0 / 128
+    x = np.arange(n) * h
+    r = 1.0 + 0.5 * np.sin(2 * np.pi * x[None, :] * 4) * np.sin(2 * np.pi * x[:, None] * 4)
+    gamma = np.zeros((n, n), np.uint8)
+    gamma[64, 64] = 1
+    uf, _, _ = O.fsm(r, gamma, 0.0, h)
+    u, st, log = O.dd(r, gamma, 0.0, h, (4, 4), 8, theta=0.2, max_iter=40, tol=1e-12, max_coarse_sweeps=8)
+    assert st["converged"] == 1
+    assert np.max(np.abs(u - uf)) < 1e-7
+
+
+def test_speedup_bound_closed_form():
+    """Sec. 4.3: the example N=20, M=100, d=2, 10 sweeps gives k << 266."""
+    line = [l for l in open(os.path.join(GOLD, "paper_numbers.txt")) if l.startswith("speedup_bound")][0]
+    kv = dict(t.split("=") for t in line.split()[1:])
+    N, M, d, C = (int(kv[k]) for k in ("N", "M", "d", "C"))
+
+    def A(n, dd):
+        return C * 2 ** dd * (n + 1) ** dd
+
+    bound = A(N * M, d) / (A(N, d) + A(M, d) + 2 ** d * M * (N + 1) ** 2)
+    assert int(bound) == int(kv["value"])
+
+
+def test_adjoint_matches_finite_differences():
+    """dJ/dr of the converged discrete system against central differences of the
+    FSM solution (J = 0.5 sum over receivers of (u - d)^2)."""
+    rng = np.random.default_rng(11)
+    n = 21
+    h = 1.0 / 20
+    r = 1.0 + 0.3 * rng.uniform(size=(n, n))
+    gamma = np.zeros((n, n), np.uint8)
+    gamma[10, 0] = 1
+    rec = [(j, n - 1) for j in range(2, n - 2, 3)]
+    d = rng.uniform(0.8, 1.2, len(rec))
+
+    def J(rr):
+        u, _, _ = O.fsm(rr, gamma, 0.0, h)
+        return 0.5 * sum((u[p] - dd) ** 2 for p, dd in zip(rec, d)), u
+
+    J0, u0 = J(r)
+    dJdu = np.zeros_like(r)
+    for p, dd in zip(rec, d):
+        dJdu[p] = u0[p] - dd
+    grad = O.adjoint(r, gamma, u0, dJdu, h)
+    cells = [(j, i) for j in range(3, n - 3, 4) for i in range(3, n - 3, 4)]
+    for c in cells:
+        e = 1e-6
+        rp = r.copy(); rp[c] += e
+        rm = r.copy(); rm[c] -= e
+        fd = (J(rp)[0] - J(rm)[0]) / (2 * e)
+        assert grad[c] == pytest.approx(fd, rel=1e-5, abs=1e-9)
