@@ -1,0 +1,147 @@
+/*
+ * eik.h -- C ABI of libeik, a GB300 (sm_103a) implementation of the two-scale
+ * domain-decomposition method for the static Eikonal boundary value problem
+ *     |grad u| = r(x) in Omega,   u = g on Gamma
+ * of Martin & Tsai, "A Multiscale Domain Decomposition Algorithm for Boundary
+ * Value Problems for Eikonal Equations" (arXiv:1805.04198).
+ *
+ * Conventions shared by every entry point:
+ *  - Every array argument is a DEVICE pointer unless a comment says "host".
+ *    The caller allocates and owns all memory; the library never allocates
+ *    device memory and never frees caller memory.
+ *  - Nodes are indexed [z][y][x] with x fastest.  Node (x, y, z) of an array
+ *    lives at element  x + y * stride[1] + z * stride[2]  (stride[0] must be 1).
+ *  - Floating-point arrays hold eik_grid.dtype values (float or double).
+ *    gamma is one byte per node (nonzero = node belongs to Gamma).
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = the
+ *    legacy default stream).  Calls return as soon as the work is enqueued;
+ *    results and device-side statistics are valid once the stream completes.
+ *  - Validation errors return EIK_EINVAL before any CUDA work is enqueued;
+ *    eik_last_error() then describes the problem (thread-local string).
+ *  - Device-side bounded waits never trap: if one expires the kernel stops,
+ *    and the `error` field of the device statistics is set to
+ *    EIK_EDEVICE_TIMEOUT.
+ *  - The discrete equation is the first-order Godunov upwind scheme of Sec. 1.1
+ *    (eq. "godonuv"), with one-sided differences at the grid boundary.
+ */
+#ifndef EIK_H
+#define EIK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { EIK_F32 = 0, EIK_F64 = 1 } eik_dtype;
+
+typedef enum {
+    EIK_OK = 0,
+    EIK_EINVAL = -1,          /* invalid argument (nothing enqueued) */
+    EIK_ENOMEM = -2,          /* workspace smaller than the size query returned */
+    EIK_ECUDA = -3,           /* a CUDA call failed (see eik_last_error) */
+    EIK_EDEVICE_TIMEOUT = -4, /* reported in the device stats: a bounded wait expired */
+    EIK_EUNSUPPORTED = -5     /* valid request this build does not implement */
+} eik_status;
+
+/* Grid description.  ndim = 2 or 3; n[a] = number of nodes along axis a
+ * (n[2] = 1 when ndim = 2); h = node spacing (same on every axis). */
+typedef struct {
+    int ndim;
+    int dtype;          /* eik_dtype */
+    int64_t n[3];
+    int64_t stride[3];  /* element strides of the caller's arrays; stride[0] = 1 */
+    double h;
+} eik_grid;
+
+/* ------------------------------------------------------------------------- */
+/* Plain fast sweeping method (Sec. 1.1, "Initialization", "Sweeping          */
+/* iterations", eq. "FSMupdate").                                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t sweeps;     /* sweeps executed */
+    int converged;      /* 1 if the last sweep changed no value */
+    int error;          /* EIK_OK or EIK_EDEVICE_TIMEOUT */
+} eik_fsm_stats;
+
+/* Workspace (bytes, device) needed by eik_fsm for this grid; 0 if invalid. */
+size_t eik_fsm_workspace_size(const eik_grid *grid);
+
+/*
+ * eik_fsm: solve the Godunov system on the whole grid by Gauss-Seidel sweeps
+ * in the 2^d orderings of Sec. 1.1 (the sign of x is the outermost loop,
+ * -1 first), with the update u = min(u, u~).  Gamma nodes are fixed at g; all
+ * other nodes start at +inf.  Stops after the first sweep that changes no value
+ * (the discrete solution) or after max_sweeps sweeps.
+ *   r      [in]  slowness, > 0 and finite at every non-Gamma node
+ *   gamma  [in]  Gamma mask;  g [in] boundary values, read where gamma != 0
+ *   u      [out] solution (unreached nodes are +inf)
+ *   ws     [in]  scratch of at least eik_fsm_workspace_size(grid) bytes,
+ *                256-byte aligned; its contents need no initialisation
+ *   stats  [out] device pointer (may be NULL)
+ * Returns EIK_OK, EIK_EINVAL, EIK_ENOMEM, EIK_ECUDA or EIK_EUNSUPPORTED.
+ */
+int eik_fsm(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, void *u,
+            int64_t max_sweeps, void *ws, size_t ws_bytes, eik_fsm_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* Two-scale domain decomposition (Sec. 3.2, Steps 1-4, Alg. 1-5).            */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int tiles[3];          /* subdomains per axis; (n[a]-1) % tiles[a] == 0 (host) */
+    int coarse_ratio;      /* c: H = c h, (n[a]-1)/tiles[a] % c == 0; c equal to the
+                              subdomain width is the paper's own construction */
+    double theta;          /* weight of the theta-parareal correction (Alg. 5) */
+    int max_iter;          /* parareal iteration cap (k of the last fine solve) */
+    double tol;            /* stop once k >= 1 and max|U^k - U^{k-1}| < tol */
+    int64_t max_fsm_sweeps;    /* cap per subdomain solve (Step 3) */
+    int64_t max_coarse_sweeps; /* cap per coarse-grid solve (Steps 1 and 4) */
+} eik_dd_params;
+
+typedef struct {
+    int iters;             /* k of the last fine solve */
+    int converged;         /* 1 if stopped by tol */
+    int error;             /* EIK_OK or EIK_EDEVICE_TIMEOUT */
+    int causal_rounds_max; /* rounds of the causal sweep (Alg. 2) until stable */
+    int64_t fsm_sweeps_max, coarse_sweeps_max;
+    int64_t fsm_cap_hits, coarse_cap_hits;
+    double last_delta;     /* max|U^k - U^{k-1}| of the last coarse update */
+} eik_dd_stats;
+
+/* Workspace (bytes, device) needed by eik_dd_solve; 0 if the request is invalid. */
+size_t eik_dd_workspace_size(const eik_grid *grid, const eik_dd_params *params);
+
+/*
+ * eik_dd_solve: the two-scale DD / theta-parareal iteration.
+ *   Step 1  every shifted coarse grid (spacing H) solved by FSM with Alg. 1,
+ *           then the causal sweep (Alg. 2)                        -> U^0, W^0
+ *   repeat for k = 0, 1, ...
+ *   Step 2  subdomain boundary data: U where W.n > 0 for an inward normal n,
+ *           otherwise free (+inf, one-sided updates); Gamma fixed at g
+ *   Step 3  FSM in every subdomain (Alg. 3)                       -> u, w
+ *   Alg. 4  u^k, w^k at every coarse-set node from the subdomain copies
+ *           stop if k == max_iter or (k >= 1 and max|U^k - U^{k-1}| < tol)
+ *   Step 4  Alg. 5 weighted update U = u^k + theta (U~ - C_H(U^k)) swept on
+ *           every shifted grid, W = w^k, then the causal sweep   -> U^{k+1}
+ * u_out receives the fine solution patched from the last subdomain solves
+ * (coarse-set nodes take the Alg. 4 value).  Hitting max_iter is not an error.
+ * params is a host pointer; stats a device pointer (may be NULL).
+ * ws: scratch of eik_dd_workspace_size() bytes, 256-byte aligned, no
+ * initialisation needed.  Returns EIK_OK, EIK_EINVAL, EIK_ENOMEM, EIK_ECUDA or
+ * EIK_EUNSUPPORTED.
+ */
+int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                 const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes,
+                 eik_dd_stats *stats, void *stream);
+
+/* Thread-local description of the last non-OK status returned on this thread. */
+const char *eik_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+int eik_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EIK_H */

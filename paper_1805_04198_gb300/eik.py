@@ -1,0 +1,217 @@
+"""Thin Python binding of libeik (include/eik.h).
+
+Argument marshalling only: every step of the solvers runs in the CUDA kernels
+of libeik.so.  PyTorch supplies device memory and the current stream.  There is
+no fallback: if libeik.so is missing or cannot be loaded, every call raises.
+
+Entry points mirror the C names:
+    eik_fsm_workspace_size, eik_fsm, eik_dd_workspace_size, eik_dd_solve,
+    eik_last_error, eik_version
+plus the conveniences :func:`fsm` and :func:`dd_solve`, which allocate the
+workspace and the output with torch and return host-side statistics.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeik.so")
+_lock = threading.Lock()
+_lib = None
+
+EIK_F32, EIK_F64 = 0, 1
+STATUS = {0: "EIK_OK", -1: "EIK_EINVAL", -2: "EIK_ENOMEM", -3: "EIK_ECUDA", -4: "EIK_EDEVICE_TIMEOUT",
+          -5: "EIK_EUNSUPPORTED"}
+
+
+class EikError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("dtype", ctypes.c_int), ("n", ctypes.c_int64 * 3),
+                ("stride", ctypes.c_int64 * 3), ("h", ctypes.c_double)]
+
+
+class FsmStats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("converged", ctypes.c_int), ("error", ctypes.c_int)]
+
+
+class DDParams(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_int * 3), ("coarse_ratio", ctypes.c_int), ("theta", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("max_fsm_sweeps", ctypes.c_int64),
+                ("max_coarse_sweeps", ctypes.c_int64)]
+
+
+class DDStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("error", ctypes.c_int),
+                ("causal_rounds_max", ctypes.c_int), ("fsm_sweeps_max", ctypes.c_int64),
+                ("coarse_sweeps_max", ctypes.c_int64), ("fsm_cap_hits", ctypes.c_int64),
+                ("coarse_cap_hits", ctypes.c_int64), ("last_delta", ctypes.c_double)]
+
+
+def _as_dict(s):
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def load():
+    """Load libeik.so (built by __graft_entry__.build()); raise if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libeik.so not found at %s: run __graft_entry__.build() first" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        lib.eik_last_error.restype = ctypes.c_char_p
+        lib.eik_version.restype = ctypes.c_int
+        lib.eik_fsm_workspace_size.restype = ctypes.c_size_t
+        lib.eik_fsm_workspace_size.argtypes = [ctypes.POINTER(Grid)]
+        lib.eik_fsm.restype = ctypes.c_int
+        lib.eik_fsm.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, vp, ctypes.c_int64, vp, ctypes.c_size_t, vp, vp]
+        lib.eik_dd_workspace_size.restype = ctypes.c_size_t
+        lib.eik_dd_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(DDParams)]
+        lib.eik_dd_solve.restype = ctypes.c_int
+        lib.eik_dd_solve.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp,
+                                     ctypes.c_size_t, vp, vp]
+        _lib = lib
+        return lib
+
+
+def eik_last_error() -> str:
+    return load().eik_last_error().decode(errors="replace")
+
+
+def eik_version() -> int:
+    return load().eik_version()
+
+
+def _check(code):
+    if code != 0:
+        raise EikError(code, eik_last_error())
+
+
+def make_grid(t: torch.Tensor, h: float) -> Grid:
+    """eik_grid describing tensor t of shape (ny, nx) or (nz, ny, nx)."""
+    if t.dim() not in (2, 3):
+        raise ValueError("expected a 2-D or 3-D tensor")
+    if t.dtype not in (torch.float32, torch.float64):
+        raise ValueError("dtype must be float32 or float64")
+    if t.stride(-1) != 1:
+        raise ValueError("innermost dimension must be contiguous")
+    d = t.dim()
+    n = list(reversed(t.shape)) + [1] * (3 - d)
+    st = list(reversed(t.stride())) + [0] * (3 - d)
+    if d == 2:
+        st[2] = st[1] * n[1]
+    return Grid(d, EIK_F64 if t.dtype == torch.float64 else EIK_F32, (ctypes.c_int64 * 3)(*n),
+                (ctypes.c_int64 * 3)(*st), float(h))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_like(ref, *ts):
+    for t in ts:
+        if t.device != ref.device or t.shape != ref.shape or t.stride() != ref.stride():
+            raise ValueError("all arrays must share device, shape and strides")
+
+
+def _workspace(nbytes, device):
+    return torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+
+
+def _aligned(ws):
+    off = (-ws.data_ptr()) % 256
+    return ctypes.c_void_p(ws.data_ptr() + off), ws.numel() - off
+
+
+def eik_fsm_workspace_size(grid: Grid) -> int:
+    return int(load().eik_fsm_workspace_size(ctypes.byref(grid)))
+
+
+def eik_fsm(grid, r, gamma, g, u, max_sweeps, ws, stats_dev, stream=None):
+    """Direct C call: all tensors on the device, ws 256-byte aligned uint8."""
+    lib = load()
+    wsp, wsn = _aligned(ws)
+    _check(lib.eik_fsm(ctypes.byref(grid), _ptr(r), _ptr(gamma), _ptr(g), _ptr(u), int(max_sweeps), wsp, wsn,
+                       _ptr(stats_dev), _stream(stream)))
+
+
+def eik_dd_workspace_size(grid: Grid, params: DDParams) -> int:
+    return int(load().eik_dd_workspace_size(ctypes.byref(grid), ctypes.byref(params)))
+
+
+def eik_dd_solve(grid, r, gamma, g, params, u_out, ws, stats_dev, stream=None):
+    lib = load()
+    wsp, wsn = _aligned(ws)
+    _check(lib.eik_dd_solve(ctypes.byref(grid), _ptr(r), _ptr(gamma), _ptr(g), ctypes.byref(params), _ptr(u_out),
+                            wsp, wsn, _ptr(stats_dev), _stream(stream)))
+
+
+def dd_params(tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
+              max_coarse_sweeps=8) -> DDParams:
+    t = list(tiles) + [1] * (3 - len(tiles))
+    return DDParams((ctypes.c_int * 3)(*t), int(coarse_ratio), float(theta), int(max_iter), float(tol),
+                    int(max_fsm_sweeps), int(max_coarse_sweeps))
+
+
+def fsm(r, gamma, g, h, max_sweeps=100000, stream=None, sync=True):
+    """Plain FSM on the whole grid.  Returns (u, stats dict)."""
+    _check_like(r, g)
+    if gamma.dtype != torch.uint8 or gamma.shape != r.shape:
+        raise ValueError("gamma must be uint8 with r's shape")
+    grid = make_grid(r, h)
+    nbytes = eik_fsm_workspace_size(grid)
+    if nbytes == 0:
+        raise EikError(-1, eik_last_error())
+    ws = _workspace(nbytes, r.device)
+    u = torch.empty_like(r)
+    st = torch.zeros(ctypes.sizeof(FsmStats), dtype=torch.uint8, device=r.device)
+    eik_fsm(grid, r, gamma.contiguous(), g, u, max_sweeps, ws, st, stream)
+    if not sync:
+        return u, st
+    s = FsmStats.from_buffer_copy(bytes(st.cpu().numpy()))
+    if s.error:
+        raise EikError(s.error, "device-side wait expired")
+    return u, _as_dict(s)
+
+
+def dd_solve(r, gamma, g, h, tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
+             max_coarse_sweeps=8, stream=None, sync=True):
+    """Two-scale DD solve (Sec. 3.2).  Returns (u, stats dict)."""
+    _check_like(r, g)
+    if gamma.dtype != torch.uint8 or gamma.shape != r.shape:
+        raise ValueError("gamma must be uint8 with r's shape")
+    grid = make_grid(r, h)
+    p = dd_params(tiles, coarse_ratio, theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps)
+    nbytes = eik_dd_workspace_size(grid, p)
+    if nbytes == 0:
+        raise EikError(-1, eik_last_error())
+    ws = _workspace(nbytes, r.device)
+    u = torch.empty_like(r)
+    st = torch.zeros(ctypes.sizeof(DDStats), dtype=torch.uint8, device=r.device)
+    eik_dd_solve(grid, r, gamma.contiguous(), g, p, u, ws, st, stream)
+    if not sync:
+        return u, st
+    s = DDStats.from_buffer_copy(bytes(st.cpu().numpy()))
+    if s.error:
+        raise EikError(s.error, "device-side wait expired")
+    return u, _as_dict(s)
+
+
+def parse_dd_stats(st: torch.Tensor) -> dict:
+    return _as_dict(DDStats.from_buffer_copy(bytes(st.cpu().numpy())))

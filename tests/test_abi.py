@@ -1,0 +1,66 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and rejects invalid requests before any CUDA work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_04198_gb300 import _build, eik
+    _build.build()
+    return eik
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "eik.h")).read()
+    declared = set(re.findall(r"\b(eik_[a-z0-9_]+)\s*\(", hdr))
+    assert {"eik_fsm", "eik_dd_solve", "eik_last_error", "eik_version"} <= declared
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(so, name), name
+
+
+def test_version(lib):
+    assert lib.eik_version() >= 100
+
+
+def _grid(lib, n=(65, 65), dtype=0, h=1 / 64, stride=None):
+    st = stride or (1, n[0], n[0] * n[1])
+    return lib.Grid(2, dtype, (ctypes.c_int64 * 3)(n[0], n[1], 1), (ctypes.c_int64 * 3)(*st), h)
+
+
+def test_workspace_sizes_and_validation(lib):
+    g = _grid(lib)
+    assert lib.eik_fsm_workspace_size(g) > 0
+    p = lib.dd_params((4, 4), 8)
+    assert lib.eik_dd_workspace_size(g, p) > 0
+    # tiles not dividing n-1
+    assert lib.eik_dd_workspace_size(g, lib.dd_params((3, 4), 8)) == 0
+    assert "tiles" in lib.eik_last_error()
+    # coarse ratio not dividing the subdomain width
+    assert lib.eik_dd_workspace_size(g, lib.dd_params((4, 4), 5)) == 0
+    assert "coarse_ratio" in lib.eik_last_error()
+    # bad spacing / dtype / stride
+    assert lib.eik_fsm_workspace_size(_grid(lib, h=0.0)) == 0
+    assert lib.eik_fsm_workspace_size(_grid(lib, dtype=7)) == 0
+    assert lib.eik_fsm_workspace_size(_grid(lib, stride=(1, 10, 650))) == 0
+    assert lib.eik_dd_workspace_size(g, lib.dd_params((4, 4), 8, max_iter=-1)) == 0
+
+
+def test_calls_reject_null_and_small_workspace(lib):
+    so = lib.load()
+    g = _grid(lib)
+    p = lib.dd_params((4, 4), 8)
+    null = ctypes.c_void_p(0)
+    rc = so.eik_dd_solve(ctypes.byref(g), null, null, null, ctypes.byref(p), null, null, 0, null, null)
+    assert rc == -1
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: rejected before use
+    rc = so.eik_dd_solve(ctypes.byref(g), fake, fake, fake, ctypes.byref(p), fake, fake, 16, null, null)
+    assert rc == -2 and "workspace" in lib.eik_last_error()
+    rc = so.eik_fsm(ctypes.byref(g), fake, fake, fake, fake, 0, fake, 1 << 30, null, null)
+    assert rc == -1

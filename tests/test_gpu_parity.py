@@ -1,0 +1,152 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 builds perform the same IEEE operations as the oracle, so their results
+are compared bitwise.  FP32 builds are compared with the oracle run on the same
+FP32-rounded inputs: relative max-norm error <= 1e-5 (the tolerance of the
+method's FP32 storage).  Winds are compared through their effect: the DD
+iterates, which depend on every Alg. 4 / Alg. 5 decision.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1805_04198_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TOL32 = 1e-5
+
+
+def _t(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def _rel(a, b):
+    fin = np.isfinite(b)
+    assert np.array_equal(np.isfinite(a), fin)
+    return np.max(np.abs(a[fin] - b[fin])) / np.max(np.abs(b[fin]))
+
+
+def _random_problem(shape, seed, nsrc=3):
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(0.5, 2.0, shape)
+    gamma = np.zeros(shape, np.uint8)
+    for _ in range(nsrc):
+        gamma[tuple(rng.integers(0, s) for s in shape)] = 1
+    g = rng.uniform(0.0, 0.1, shape)
+    return r, gamma, g
+
+
+@pytest.mark.parametrize("shape", [(33, 33), (70, 100), (5, 200), (129, 40), (1, 1)])
+def test_fsm_fp64_bitwise(gpu, shape):
+    if shape == (1, 1):
+        pytest.skip("degenerate 1x1 grid is rejected by validation (n >= 2)")
+    r, gamma, g = _random_problem(shape, sum(shape))
+    u_ref, s_ref, _ = O.fsm(r, gamma, g, 0.05)
+    u, st = gpu.fsm(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), 0.05)
+    assert st["converged"] == 1
+    np.testing.assert_array_equal(u.cpu().numpy(), u_ref)
+
+
+def test_fsm_sweep_cap_matches_oracle(gpu):
+    """Stopped early by max_sweeps: the same sweeps in the same order."""
+    r, gamma, g = _random_problem((60, 90), 5, nsrc=1)
+    for k in (1, 2, 3, 5):
+        u_ref, s_ref, c_ref = O.fsm(r, gamma, g, 0.05, max_sweeps=k)
+        u, st = gpu.fsm(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), 0.05, max_sweeps=k)
+        assert st["sweeps"] == s_ref
+        np.testing.assert_array_equal(u.cpu().numpy(), u_ref)
+
+
+def test_fsm_fp32(gpu):
+    shape = (97, 257)
+    r, gamma, g = _random_problem(shape, 9)
+    r32 = r.astype(np.float32)
+    g32 = g.astype(np.float32)
+    u_ref, _, _ = O.fsm(r32.astype(np.float64), gamma, g32.astype(np.float64), 1.0 / 256)
+    u, st = gpu.fsm(_t(r32, torch.float32), _t(gamma, torch.uint8), _t(g32, torch.float32), 1.0 / 256)
+    assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
+
+
+def _dd_case(n, tiles, c, amp=0.5, eps=0.25, src=None):
+    h = 1.0 / (n - 1)
+    r = I.sin_product((n, n), h, amp, eps)
+    gamma, g = I.point_source((n, n), src if src is not None else (n // 2, n // 2))
+    return r, gamma, g, h
+
+
+@pytest.mark.parametrize("n,tiles,c,theta,kmax", [
+    (65, (4, 4), 8, 0.2, 6),
+    (65, (4, 4), 16, 0.5, 4),     # c equal to the subdomain width (the paper's setting)
+    (65, (2, 4), 8, 1.0, 3),      # theta = 1, anisotropic tiling
+    (97, (3, 3), 16, 0.2, 5),     # 33-node subdomains: two blocks, ragged tail
+    (129, (2, 2), 8, 0.3, 4),     # 65-node subdomains, c < S
+])
+def test_dd_fp64_bitwise(gpu, n, tiles, c, theta, kmax):
+    r, gamma, g, h = _dd_case(n, tiles, c)
+    for k in range(kmax + 1):
+        u_ref, s_ref, _ = O.dd(r, gamma, g, h, tiles, c, theta=theta, max_iter=k, tol=0.0, max_coarse_sweeps=8)
+        u, st = gpu.dd_solve(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h, tiles, c,
+                             theta=theta, max_iter=k, tol=0.0, max_coarse_sweeps=8)
+        assert st["iters"] == s_ref["iters"] == k
+        assert st["fsm_sweeps_max"] <= s_ref["fsm_sweeps_max"] + 4
+        np.testing.assert_array_equal(u.cpu().numpy(), u_ref, err_msg="k=%d" % k)
+
+
+def test_dd_fp64_tol_stop_and_stats(gpu):
+    r, gamma, g, h = _dd_case(65, (4, 4), 8, amp=0.3)
+    u_ref, s_ref, log = O.dd(r, gamma, g, h, (4, 4), 8, theta=0.2, max_iter=40, tol=1e-9, max_coarse_sweeps=8)
+    u, st = gpu.dd_solve(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h, (4, 4), 8,
+                         theta=0.2, max_iter=40, tol=1e-9, max_coarse_sweeps=8)
+    assert st["converged"] == s_ref["converged"] == 1
+    assert st["iters"] == s_ref["iters"]
+    assert st["last_delta"] == s_ref["last_delta"]
+    assert st["coarse_cap_hits"] == s_ref["coarse_cap_hits"]
+    np.testing.assert_array_equal(u.cpu().numpy(), u_ref)
+
+
+def test_dd_model_problem_theorem1(gpu):
+    """Theorem 1 setting through the GPU path: bitwise equal to the oracle,
+    which itself reproduces u^f on columns i <= k."""
+    N, M = 8, 16
+    h = 1.0 / (N * M)
+    nx, ny = N * M + 1, M + 1
+    x = np.arange(nx) * h
+    y = np.arange(ny) * h
+    r = np.ones((ny, nx))
+    gamma = np.zeros((ny, nx), np.uint8)
+    gamma[0, :] = 1
+    gamma[:, 0] = 1
+    g = np.sqrt(x[None, :] ** 2 + y[:, None] ** 2)
+    for k in (0, 3, 8):
+        u_ref, _, _ = O.dd(r, gamma, g, h, (N, 1), M, theta=1.0, max_iter=k, tol=-1.0)
+        u, _ = gpu.dd_solve(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h, (N, 1), M,
+                            theta=1.0, max_iter=k, tol=-1.0)
+        np.testing.assert_array_equal(u.cpu().numpy(), u_ref)
+
+
+def test_dd_c0_config_fp64(gpu):
+    """257^2, eps = 1/16, point source at the centre, 4x4 subdomains, coarse
+    ratio 8 (33^2 coarse grid), theta = 1, 10 iterations, FP64."""
+    w = I.workload_c0()
+    args = dict(theta=w["theta"], max_iter=w["max_iter"], tol=w["tol"], max_coarse_sweeps=8)
+    u_ref, s_ref, _ = O.dd(w["r"], w["gamma"], w["g"], w["h"], w["tiles"], w["c"], **args)
+    u, st = gpu.dd_solve(_t(w["r"], torch.float64), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float64),
+                         w["h"], w["tiles"], w["c"], **args)
+    assert st["iters"] == s_ref["iters"]
+    np.testing.assert_array_equal(u.cpu().numpy(), u_ref)
+
+
+def test_dd_fp32_converged_against_oracle(gpu):
+    """FP32 storage: the converged DD output agrees with the FP64 oracle on the
+    same rounded inputs within 1e-5 relative max-norm."""
+    r, gamma, g, h = _dd_case(129, (4, 4), 8, amp=0.5, eps=0.25)
+    r32 = r.astype(np.float32)
+    args = dict(theta=0.2, max_iter=40, tol=1e-7, max_coarse_sweeps=8)
+    u_ref, s_ref, _ = O.dd(r32.astype(np.float64), gamma, g, h, (4, 4), 8, **args)
+    u, st = gpu.dd_solve(_t(r32, torch.float32), _t(gamma, torch.uint8), _t(g, torch.float32), h, (4, 4), 8,
+                         **args)
+    assert s_ref["converged"] == 1
+    assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
