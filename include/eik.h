@@ -63,6 +63,8 @@ typedef struct {
     int64_t sweeps;     /* sweeps executed */
     int converged;      /* 1 if the last sweep changed no value */
     int error;          /* EIK_OK or EIK_EDEVICE_TIMEOUT */
+    int64_t updates;    /* Godunov local solves executed */
+    int64_t launches;   /* kernels enqueued by this call */
 } eik_fsm_stats;
 
 /* Workspace (bytes, device) needed by eik_fsm for this grid; 0 if invalid. */
@@ -107,6 +109,9 @@ typedef struct {
     int64_t fsm_sweeps_max, coarse_sweeps_max;
     int64_t fsm_cap_hits, coarse_cap_hits;
     double last_delta;     /* max|U^k - U^{k-1}| of the last coarse update */
+    int64_t fine_updates;  /* Godunov local solves executed in the subdomains (Step 3) */
+    int64_t coarse_updates;/* local solves executed on the coarse grids (Steps 1, 4) */
+    int64_t launches;      /* kernels enqueued by this call */
 } eik_dd_stats;
 
 /* Workspace (bytes, device) needed by eik_dd_solve; 0 if the request is invalid. */
@@ -134,6 +139,27 @@ size_t eik_dd_workspace_size(const eik_grid *grid, const eik_dd_params *params);
 int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
                  const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes,
                  eik_dd_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* Optional per-kernel timing (a benchmarking aid, off by default).  While     */
+/* enabled, every kernel the library launches is bracketed by two CUDA events  */
+/* recorded on the launch's own stream.  Not thread-safe; enable it only when  */
+/* one host thread drives the library.                                         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    const char *name;   /* static string owned by the library */
+    int64_t launches;
+    double total_ms;    /* sum of event-measured launch durations */
+    double max_ms;
+} eik_kernel_time;
+
+/* Turns event bracketing on (on != 0) or off.  Returns the previous state. */
+int eik_profile_enable(int on);
+
+/* Waits for every recorded event, writes up to max_entries per-kernel totals
+ * (host array) and clears the record.  Returns the number of kernels with at
+ * least one timed launch (may exceed max_entries), or EIK_ECUDA. */
+int eik_profile_collect(eik_kernel_time *out, int max_entries);
 
 /* Thread-local description of the last non-OK status returned on this thread. */
 const char *eik_last_error(void);

@@ -24,6 +24,15 @@ template <> struct Num<float> {
     static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
     static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    // Square root used inside the local solve.  FP32 storage carries a 1e-5
+    // accuracy budget, so the single-instruction hardware approximation
+    // (relative error ~1e-7, applied only to the increment of the two-term
+    // branch) is used; FP64 keeps the correctly rounded root.
+    static __device__ __forceinline__ float sqrt_solve(float a) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
 };
 
 template <> struct Num<double> {
@@ -33,6 +42,7 @@ template <> struct Num<double> {
     static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
     static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    static __device__ __forceinline__ double sqrt_solve(double a) { return __dsqrt_rn(a); }
 };
 
 // Wind packing: component a in {-1,0,+1} stored as (w+1) in 2 bits at 2a.
@@ -47,28 +57,25 @@ constexpr uint8_t WIND_ZERO = 0x15;  // (0,0,0)
 // 2-D Godunov local solve.  vm*/vp* are the neighbours on the minus/plus side
 // of each axis (+inf where missing: the one-sided rule of Sec. 1.1).  Returns
 // u~ and the packed wind of the branch taken (zero wind when u~ is +inf).
+// Both branches are evaluated and one is selected, so no warp diverges; the
+// selected branch performs exactly the operations written in the paper's
+// closed form.
 template <class T>
 __device__ __forceinline__ T local_solve2(T vmx, T vpx, T vmy, T vpy, T rh, uint8_t &wind) {
     using N = Num<T>;
-    T a, b;
-    int sa, sb;
     // Alg. 3: the smaller neighbour per axis; a tie goes to the plus side.
-    if (vmx < vpx) { a = vmx; sa = 1; } else { a = vpx; sa = -1; }
-    if (vmy < vpy) { b = vmy; sb = 1; } else { b = vpy; sb = -1; }
-    T d = N::sub(a, b);
-    T u;
-    if (fabs(d) < rh) {
-        // two-term branch: (a + b + sqrt(2 r^2 h^2 - (a-b)^2)) / 2
-        T disc = N::sub(N::mul(N::mul(T(2), rh), rh), N::mul(d, d));
-        u = N::mul(N::add(N::add(a, b), N::sqrt_(disc)), T(0.5));
-        wind = wind_pack(sa, sb);
-    } else if (a < b) {
-        u = N::add(a, rh);
-        wind = (u < N::inf()) ? wind_pack(sa, 0) : WIND_ZERO;
-    } else {
-        u = N::add(b, rh);
-        wind = (u < N::inf()) ? wind_pack(0, sb) : WIND_ZERO;
-    }
+    const bool lx = vmx < vpx, ly = vmy < vpy;
+    const T a = lx ? vmx : vpx, b = ly ? vmy : vpy;
+    const int sa = lx ? 1 : -1, sb = ly ? 1 : -1;
+    const T d = N::sub(a, b);
+    // two-term branch: (a + b + sqrt(2 r^2 h^2 - (a-b)^2)) / 2
+    const T disc = N::sub(N::mul(N::mul(T(2), rh), rh), N::mul(d, d));
+    const T u2 = N::mul(N::add(N::add(a, b), N::sqrt_solve(fmax(disc, T(0)))), T(0.5));
+    const bool two = fabs(d) < rh;
+    const bool ax = a < b;
+    const T u1 = N::add(ax ? a : b, rh);
+    const T u = two ? u2 : u1;
+    wind = two ? wind_pack(sa, sb) : (u < N::inf() ? (ax ? wind_pack(sa, 0) : wind_pack(0, sb)) : WIND_ZERO);
     return u;
 }
 
@@ -77,14 +84,13 @@ __device__ __forceinline__ T local_solve2(T vmx, T vpx, T vmy, T vpy, T rh, uint
 template <class T>
 __device__ __forceinline__ T local_solve2_value(T vmx, T vpx, T vmy, T vpy, T rh) {
     using N = Num<T>;
-    T a = fmin(vmx, vpx);
-    T b = fmin(vmy, vpy);
-    T d = N::sub(a, b);
-    if (fabs(d) < rh) {
-        T disc = N::sub(N::mul(N::mul(T(2), rh), rh), N::mul(d, d));
-        return N::mul(N::add(N::add(a, b), N::sqrt_(disc)), T(0.5));
-    }
-    return N::add(fmin(a, b), rh);
+    const T a = fmin(vmx, vpx);
+    const T b = fmin(vmy, vpy);
+    const T d = N::sub(a, b);
+    const T disc = N::sub(N::mul(N::mul(T(2), rh), rh), N::mul(d, d));
+    const T u2 = N::mul(N::add(N::add(a, b), N::sqrt_solve(fmax(disc, T(0)))), T(0.5));
+    const T u1 = N::add(fmin(a, b), rh);
+    return fabs(d) < rh ? u2 : u1;
 }
 
 // Status codes mirrored from eik.h for device code.

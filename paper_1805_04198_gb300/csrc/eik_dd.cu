@@ -26,11 +26,13 @@
 #include "dd_geom.cuh"
 #include "engine.cuh"
 #include "host_util.h"
+#include "prof.h"
 
 namespace eik {
 
 struct DevStats {
     unsigned long long fsm_sweeps_max, coarse_sweeps_max, fsm_caps, coarse_caps;
+    unsigned long long fine_updates, coarse_updates;
     int causal_rounds_max;
     int err;
     int iters;
@@ -78,28 +80,18 @@ __device__ __forceinline__ T fine_at(const T *a, long long sy, int X, int Y) {
 // Engine policies
 // --------------------------------------------------------------------------
 
-// FSM update u = min(u, u~) (Sec. 1.1, eq. FSMupdate).  Statics: r (<= 0 marks
-// a fixed node).  `face` (may be null) marks Dirichlet subdomain-boundary nodes.
+// FSM update u = min(u, u~) (Sec. 1.1, eq. FSMupdate).  Statics: r, stored
+// as a non-positive value at fixed nodes (Gamma, Dirichlet boundary data).
 template <class T>
 struct FsmPolicy {
     T h;
-    const uint8_t *face;
-    int nx, ny;
-    __device__ __forceinline__ T update(T self, T vmx, T vpx, T vmy, T vpy, const T *sv, uint8_t, int x, int y,
+    __device__ __forceinline__ T update(T self, T vmx, T vpx, T vmy, T vpy, const T *sv, uint8_t,
                                         bool &changed) const {
         const T r = sv[0];
-        if (!(r > T(0))) return self;
-        if (face) {
-            if ((x == 0 && face[y]) || (x == nx - 1 && face[ny + y]) || (y == 0 && face[2 * ny + x]) ||
-                (y == ny - 1 && face[2 * ny + nx + x]))
-                return self;
-        }
         const T ut = local_solve2_value(vmx, vpx, vmy, vpy, Num<T>::mul(r, h));
-        if (ut < self) {
-            changed = true;
-            return ut;
-        }
-        return self;
+        const bool take = (r > T(0)) && (ut < self);
+        changed = take;
+        return take ? ut : self;
     }
 };
 
@@ -110,10 +102,9 @@ struct FsmPolicy {
 template <class T>
 struct Alg5Policy {
     T H, theta;
-    __device__ __forceinline__ T update(T self, T vmx, T vpx, T vmy, T vpy, const T *sv, uint8_t mask, int, int,
+    __device__ __forceinline__ T update(T self, T vmx, T vpx, T vmy, T vpy, const T *sv, uint8_t mask,
                                         bool &changed) const {
         using N = Num<T>;
-        if (mask & 1) return self;
         uint8_t w;
         const T Ut = local_solve2(vmx, vpx, vmy, vpy, N::mul(sv[0], H), w);
         const T uk = sv[1], cold = sv[2];
@@ -121,8 +112,9 @@ struct Alg5Policy {
         bool pass = (Ut < N::inf()) && (cold < N::inf());
         pass = pass && ((wx <= 0 && (mask & 2)) || (wx >= 0 && (mask & 4)));
         pass = pass && ((wy <= 0 && (mask & 8)) || (wy >= 0 && (mask & 16)));
-        const T nu = pass ? N::add(uk, N::mul(theta, N::sub(Ut, cold))) : uk;
-        if (!(nu == self)) changed = true;
+        const T nu0 = pass ? N::add(uk, N::mul(theta, N::sub(Ut, cold))) : uk;
+        const T nu = (mask & 1) ? self : nu0;
+        changed = !(nu == self);
         return nu;
     }
 };
@@ -197,8 +189,7 @@ __device__ void grid_winds(const DDArgs<T> &A, const GridDesc &d, T Hs) {
 
 // Step 1: FSM with Alg. 1 on every shifted grid; Gamma nodes fixed at g.
 template <class T>
-__global__ void k_step1(DDArgs<T> A) {
-    extern __shared__ __align__(16) char smem[];
+__device__ __forceinline__ void k_step1_body(DDArgs<T> &A, char *smem) {
     const DDGeom &G = A.G;
     const GridDesc d = grid_desc(G, blockIdx.x);
     const size_t n = (size_t)d.nb * d.my * 32;
@@ -212,22 +203,22 @@ __global__ void k_step1(DDArgs<T> A) {
     bx.ny = d.my;
     bx.nb = d.nb;
     bx.nstepp = d.nstepp;
-    FsmPolicy<T> pol{T(G.H), nullptr, d.mx, d.my};
+    FsmPolicy<T> pol{T(G.H)};
     long long sweeps;
     bool conv;
     engine_run<T, 1, false>(bx, pol, A.max_coarse, smem, sweeps, conv, &A.st->err);
     if (threadIdx.x == 0) {
         atomicMax(&A.st->coarse_sweeps_max, (unsigned long long)sweeps);
         if (!conv) atomicAdd(&A.st->coarse_caps, 1ull);
+        atomicAdd(&A.st->coarse_updates, (unsigned long long)sweeps * d.mx * d.my);
     }
     grid_winds(A, d, T(G.H));
 }
 
 // Step 4: Alg. 5 on every shifted grid.
 template <class T>
-__global__ void k_step4(DDArgs<T> A) {
+__device__ __forceinline__ void k_step4_body(DDArgs<T> &A, char *smem) {
     if (*A.done) return;
-    extern __shared__ __align__(16) char smem[];
     const DDGeom &G = A.G;
     const GridDesc d = grid_desc(G, blockIdx.x);
     const T INF = Num<T>::inf();
@@ -273,6 +264,7 @@ __global__ void k_step4(DDArgs<T> A) {
     if (threadIdx.x == 0) {
         atomicMax(&A.st->coarse_sweeps_max, (unsigned long long)sweeps);
         if (!conv) atomicAdd(&A.st->coarse_caps, 1ull);
+        atomicAdd(&A.st->coarse_updates, (unsigned long long)sweeps * d.mx * d.my);
     }
     // W = w^k
     for (size_t e = threadIdx.x; e < n; e += blockDim.x) A.W[d.off + e] = A.wk[d.off + e];
@@ -356,7 +348,7 @@ __device__ bool causal_line(const DDArgs<T> &A, bool horizontal, int line, int r
             }
         }
         if (ff) v = fmax(v, carry);
-        if (valid && !(v == u)) {
+        if (valid && v > u) {  // values only rise; NaN never counts as a change
             A.U[a] = v;
             changed = true;
         }
@@ -418,16 +410,15 @@ __device__ __forceinline__ bool tile_inflow(const DDArgs<T> &A, int xl, int yl, 
 }
 
 template <class T>
-__global__ void k_fine(DDArgs<T> A) {
+__device__ __forceinline__ void k_fine_body(DDArgs<T> &A, char *smem) {
     if (*A.done) return;
-    extern __shared__ __align__(16) char smem[];
     const DDGeom &G = A.G;
     const T INF = Num<T>::inf();
     const int tile = blockIdx.x;
     const int tx = tile % G.tx, ty = tile / G.tx;
     const int NX = G.tnx, NY = G.tny;
     T *ut = A.tile_state + (size_t)tile * G.tile_elems;
-    uint8_t *face = reinterpret_cast<uint8_t *>(smem + engine_smem_bytes<T>(G.tnb, NY));
+    T *rsk = A.tile_rsk + (size_t)tile * G.tile_sk_elems;
     // Step 2: boundary data.  Interior and outflow nodes start at +inf.
     for (size_t e = threadIdx.x; e < G.tile_elems; e += blockDim.x) {
         int b = (int)(e / ((size_t)NY * 32));
@@ -442,6 +433,8 @@ __global__ void k_fine(DDArgs<T> A) {
         }
         ut[e] = v;
     }
+    // fixed-node marks of the face nodes for this iteration: Dirichlet (inflow)
+    // and Gamma nodes carry a non-positive slowness in the skewed statics
     for (int f = threadIdx.x; f < 2 * NY + 2 * NX; f += blockDim.x) {
         int xl, yl;
         if (f < NY) { xl = 0; yl = f; }
@@ -450,7 +443,9 @@ __global__ void k_fine(DDArgs<T> A) {
         else { xl = f - 2 * NY - NX; yl = NY - 1; }
         int X = tx * G.sx + xl, Y = ty * G.sy + yl;
         size_t ca;
-        face[f] = (!A.gamma[(size_t)Y * A.sy + X] && tile_inflow(A, xl, yl, X, Y, ca)) ? 1 : 0;
+        const bool fixed = A.gamma[(size_t)Y * A.sy + X] || tile_inflow(A, xl, yl, X, Y, ca);
+        const T v = fixed ? T(-1) : fine_at(A.r, A.sy, X, Y);
+        for (int dd = 0; dd < 4; ++dd) rsk[skew_index(dd, xl, yl, G.tnb, NY, G.tnstepp)] = v;
     }
     __threadfence_block();
     __syncthreads();
@@ -463,13 +458,14 @@ __global__ void k_fine(DDArgs<T> A) {
     bx.ny = NY;
     bx.nb = G.tnb;
     bx.nstepp = G.tnstepp;
-    FsmPolicy<T> pol{T(G.h), face, NX, NY};
+    FsmPolicy<T> pol{T(G.h)};
     long long sweeps;
     bool conv;
     engine_run<T, 1, false>(bx, pol, A.max_fsm, smem, sweeps, conv, &A.st->err);
     if (threadIdx.x == 0) {
         atomicMax(&A.st->fsm_sweeps_max, (unsigned long long)sweeps);
         if (!conv) atomicAdd(&A.st->fsm_caps, 1ull);
+        atomicAdd(&A.st->fine_updates, (unsigned long long)sweeps * NX * NY);
     }
     // outputs: copies (u, w) at coarse-set nodes, fine values elsewhere
     for (size_t e = threadIdx.x; e < G.tile_elems; e += blockDim.x) {
@@ -508,6 +504,33 @@ __global__ void k_fine(DDArgs<T> A) {
         A.cw[(size_t)slot * G.coarse_elems + ca] = w;
     }
 }
+
+// Kernel entry points.  Register caps keep two 9-warp subdomain CTAs per SM in
+// FP32 and let a 9-warp coarse-grid CTA fit the register file in FP64.
+#define EIK_KERNEL_PAIR(name, RF, RD)                                                  \
+    __global__ void __maxnreg__(RF) name##_f32(DDArgs<float> A) {                     \
+        extern __shared__ __align__(16) char smem[];                                  \
+        name##_body<float>(A, smem);                                                  \
+    }                                                                                 \
+    __global__ void __maxnreg__(RD) name##_f64(DDArgs<double> A) {                    \
+        extern __shared__ __align__(16) char smem[];                                  \
+        name##_body<double>(A, smem);                                                 \
+    }
+EIK_KERNEL_PAIR(k_step1, 96, 224)
+EIK_KERNEL_PAIR(k_step4, 160, 224)
+EIK_KERNEL_PAIR(k_fine, 96, 224)
+
+template <class T> struct DDKernels;
+template <> struct DDKernels<float> {
+    static constexpr void (*step1)(DDArgs<float>) = k_step1_f32;
+    static constexpr void (*step4)(DDArgs<float>) = k_step4_f32;
+    static constexpr void (*fine)(DDArgs<float>) = k_fine_f32;
+};
+template <> struct DDKernels<double> {
+    static constexpr void (*step1)(DDArgs<double>) = k_step1_f64;
+    static constexpr void (*step4)(DDArgs<double>) = k_step4_f64;
+    static constexpr void (*fine)(DDArgs<double>) = k_fine_f64;
+};
 
 // --------------------------------------------------------------------------
 // Alg. 4 + inputs of Alg. 5
@@ -630,7 +653,7 @@ __global__ void k_init_stats(DDArgs<T> A) {
 }
 
 template <class T>
-__global__ void k_finalize(DDArgs<T> A, eik_dd_stats *out) {
+__global__ void k_finalize(DDArgs<T> A, eik_dd_stats *out, long long launches) {
     if (threadIdx.x != 0 || !out) return;
     out->iters = A.st->iters;
     out->converged = A.st->converged;
@@ -642,6 +665,9 @@ __global__ void k_finalize(DDArgs<T> A, eik_dd_stats *out) {
     out->coarse_cap_hits = (int64_t)A.st->coarse_caps;
     const int k = A.st->iters;
     out->last_delta = k >= 1 ? A.deltas[k] : INFINITY;
+    out->fine_updates = (int64_t)A.st->fine_updates;
+    out->coarse_updates = (int64_t)A.st->coarse_updates;
+    out->launches = launches;
 }
 
 // --------------------------------------------------------------------------
@@ -650,7 +676,7 @@ __global__ void k_finalize(DDArgs<T> A, eik_dd_stats *out) {
 struct DDPlan {
     DDGeom G;
     size_t bytes;
-    size_t fine_smem, grid_smem;
+    size_t fine_smem, step1_smem, step4_smem;
     int grid_threads;
 };
 
@@ -686,8 +712,9 @@ static bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
             return false;
         }
     }
-    if (p->max_iter < 0 || p->max_fsm_sweeps < 1 || p->max_coarse_sweeps < 1) {
-        set_error("max_iter must be >= 0 and sweep caps >= 1");
+    if (p->max_iter < 0 || p->max_iter > 100000 || p->max_fsm_sweeps < 1 || p->max_coarse_sweeps < 1 ||
+        p->max_fsm_sweeps > MAX_SWEEPS || p->max_coarse_sweeps > MAX_SWEEPS) {
+        set_error("max_iter must be in [0, 100000] and sweep caps in [1, %lld]", MAX_SWEEPS);
         return false;
     }
     if (!(std::isfinite(p->theta))) {
@@ -750,16 +777,19 @@ static size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
 static DDPlan dd_plan(const eik_grid *grid, const eik_dd_params *p) {
     DDPlan P;
     P.G = make_geom((int)grid->n[0], (int)grid->n[1], p->tiles[0], p->tiles[1], p->coarse_ratio, grid->h);
+    P.step1_smem = P.step4_smem = 0;
     P.bytes = grid->dtype == EIK_F64 ? dd_layout<double>(P, nullptr, nullptr, p->max_iter)
                                      : dd_layout<float>(P, nullptr, nullptr, p->max_iter);
     const int gnb = ceil32(P.G.ncx + 1);
     P.grid_threads = 32 * gnb;
     if (grid->dtype == EIK_F64) {
-        P.fine_smem = engine_smem_bytes<double>(P.G.tnb, P.G.tny) + 2 * P.G.tnx + 2 * P.G.tny + 16;
-        P.grid_smem = engine_smem_bytes<double>(gnb, P.G.ncy + 1);
+        P.fine_smem = engine_smem_bytes<double, 1, false>(P.G.tnb, P.G.tny);
+        P.step1_smem = engine_smem_bytes<double, 1, false>(gnb, P.G.ncy + 1);
+        P.step4_smem = engine_smem_bytes<double, 3, true>(gnb, P.G.ncy + 1);
     } else {
-        P.fine_smem = engine_smem_bytes<float>(P.G.tnb, P.G.tny) + 2 * P.G.tnx + 2 * P.G.tny + 16;
-        P.grid_smem = engine_smem_bytes<float>(gnb, P.G.ncy + 1);
+        P.fine_smem = engine_smem_bytes<float, 1, false>(P.G.tnb, P.G.tny);
+        P.step1_smem = engine_smem_bytes<float, 1, false>(gnb, P.G.ncy + 1);
+        P.step4_smem = engine_smem_bytes<float, 3, true>(gnb, P.G.ncy + 1);
     }
     return P;
 }
@@ -792,17 +822,18 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     if ((rc = cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr"))) return rc;
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((int)P.fine_smem > smem_optin || (int)P.grid_smem > smem_optin) {
-        set_error("shared memory need (%zu, %zu) exceeds the device limit %d", P.fine_smem, P.grid_smem, smem_optin);
+    if ((int)P.fine_smem > smem_optin || (int)P.step1_smem > smem_optin || (int)P.step4_smem > smem_optin) {
+        set_error("shared memory need (%zu, %zu, %zu) exceeds the device limit %d", P.fine_smem, P.step1_smem,
+                  P.step4_smem, smem_optin);
         return EIK_EUNSUPPORTED;
     }
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_fine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.fine_smem),
+    if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::fine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.fine_smem),
                          "smem attr fine")))
         return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_step1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grid_smem),
+    if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.step1_smem),
                          "smem attr step1")))
         return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_step4<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grid_smem),
+    if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::step4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.step4_smem),
                          "smem attr step4")))
         return rc;
     // causal sweep: cooperative grid sized to what is co-resident
@@ -820,26 +851,32 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     const size_t tiles_nodes = (size_t)ntiles * G.tnx * G.tny;
     const int tb = (int)std::min<size_t>((tiles_nodes + ew - 1) / ew, (size_t)nsm * 16);
 
-    k_init_stats<T><<<1, 256, 0, s>>>(A);
-    k_pack_tiles<T><<<tb, ew, 0, s>>>(A);
-    k_pack_coarse<T><<<eb, ew, 0, s>>>(A);
-    k_step1<T><<<G.ngrids, P.grid_threads, P.grid_smem, s>>>(A);
+    long long nl = 0;
+    EIK_LAUNCH("dd_init", s, k_init_stats<T><<<1, 256, 0, s>>>(A)); ++nl;
+    EIK_LAUNCH("dd_pack_tiles", s, k_pack_tiles<T><<<tb, ew, 0, s>>>(A)); ++nl;
+    EIK_LAUNCH("dd_pack_coarse", s, k_pack_coarse<T><<<eb, ew, 0, s>>>(A)); ++nl;
+    EIK_LAUNCH("dd_step1_coarse_fsm", s, DDKernels<T>::step1<<<G.ngrids, P.grid_threads, P.step1_smem, s>>>(A)); ++nl;
     auto launch_causal = [&](int only) -> int {
         void *args[] = {&A, &only};
-        return cuda_check(cudaLaunchCooperativeKernel((void *)k_causal<T>, causal_blocks, causal_threads, args, 0, s),
-                          "causal launch");
+        int tok = prof_begin("dd_causal_sweep", s);
+        int r2 = cuda_check(cudaLaunchCooperativeKernel((void *)k_causal<T>, causal_blocks, causal_threads, args, 0, s),
+                            "causal launch");
+        prof_end(tok, s);
+        ++nl;
+        return r2;
     };
     if ((rc = launch_causal(0))) return rc;
     for (int k = 0; k <= p->max_iter; ++k) {
-        k_fine<T><<<ntiles, 32 * G.tnb, P.fine_smem, s>>>(A);
-        k_alg4<T><<<eb, ew, 0, s>>>(A);
-        k_check<T><<<1, 1, 0, s>>>(A, k);
+        EIK_LAUNCH("dd_fine_subdomains", s, DDKernels<T>::fine<<<ntiles, 32 * G.tnb, P.fine_smem, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd_alg4_restrict", s, k_alg4<T><<<eb, ew, 0, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd_check", s, k_check<T><<<1, 1, 0, s>>>(A, k)); ++nl;
         if (k == p->max_iter) break;
-        k_step4<T><<<G.ngrids, P.grid_threads, P.grid_smem, s>>>(A);
+        EIK_LAUNCH("dd_step4_weighted", s, DDKernels<T>::step4<<<G.ngrids, P.grid_threads, P.step4_smem, s>>>(A)); ++nl;
         if ((rc = launch_causal(1))) return rc;
-        k_delta<T><<<eb, ew, 0, s>>>(A, k);
+        EIK_LAUNCH("dd_delta", s, k_delta<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
     }
-    k_finalize<T><<<1, 32, 0, s>>>(A, stats);
+    ++nl;
+    EIK_LAUNCH("dd_finalize", s, k_finalize<T><<<1, 32, 0, s>>>(A, stats, nl));
     return cuda_check(cudaGetLastError(), "dd launch");
 }
 

@@ -12,10 +12,47 @@
 #include "common.cuh"
 #include "engine.cuh"
 #include "host_util.h"
+#include "prof.h"
+
+#include <string>
+#include <vector>
 
 namespace eik {
 
 static thread_local char g_err[512];
+
+// ---- optional per-launch event timing -------------------------------------
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_prof_pool;
+
+static cudaEvent_t prof_event() {
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int prof_begin(const char *name, cudaStream_t s) {
+    if (!g_prof_on) return -1;
+    ProfRec r{name, prof_event(), prof_event()};
+    cudaEventRecord(r.a, s);
+    g_prof.push_back(r);
+    return (int)g_prof.size() - 1;
+}
+
+void prof_end(int token, cudaStream_t s) {
+    if (token < 0) return;
+    cudaEventRecord(g_prof[token].b, s);
+}
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -48,16 +85,13 @@ struct FsmArgs {
 template <class T>
 struct PlainFsmPolicy {
     T h;
-    __device__ __forceinline__ T update(T self, T vmx, T vpx, T vmy, T vpy, const T *sv, uint8_t, int, int,
+    __device__ __forceinline__ T update(T self, T vmx, T vpx, T vmy, T vpy, const T *sv, uint8_t,
                                         bool &changed) const {
-        const T r = sv[0];
-        if (!(r > T(0))) return self;  // Gamma
+        const T r = sv[0];  // <= 0 on Gamma
         const T ut = local_solve2_value(vmx, vpx, vmy, vpy, Num<T>::mul(r, h));
-        if (ut < self) {
-            changed = true;
-            return ut;
-        }
-        return self;
+        const bool take = (r > T(0)) && (ut < self);
+        changed = take;
+        return take ? ut : self;
     }
 };
 
@@ -109,6 +143,8 @@ __global__ void k_fsm_unpack(FsmArgs<T> A, eik_fsm_stats *out) {
         out->sweeps = (int64_t)A.dev->sweeps;
         out->converged = A.dev->converged;
         out->error = A.dev->err;
+        out->updates = (int64_t)A.dev->sweeps * A.nx * A.ny;
+        out->launches = 3;
     }
 }
 
@@ -137,7 +173,8 @@ static bool fsm_plan(const eik_grid *grid, FsmPlan &P) {
     P.ny = (int)grid->n[1];
     P.nb = ceil32(P.nx);
     P.nstepp = nstep_padded(P.ny);
-    P.smem = grid->dtype == EIK_F64 ? engine_smem_bytes<double>(P.nb, P.ny) : engine_smem_bytes<float>(P.nb, P.ny);
+    P.smem = grid->dtype == EIK_F64 ? engine_smem_bytes<double, 1, false>(P.nb, P.ny)
+                                     : engine_smem_bytes<float, 1, false>(P.nb, P.ny);
     P.bytes = grid->dtype == EIK_F64 ? fsm_layout<double>(P, nullptr, nullptr) : fsm_layout<float>(P, nullptr, nullptr);
     return true;
 }
@@ -164,7 +201,9 @@ static int fsm_run(const eik_grid *grid, const FsmPlan &P, const void *r, const 
     if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if ((int)P.smem > optin || P.nb > 32) {
+    cudaFuncAttributes fa;
+    if ((rc = cuda_check(cudaFuncGetAttributes(&fa, k_fsm_run<T>), "func attr"))) return rc;
+    if ((int)P.smem > optin || P.nb > 32 || (long long)fa.numRegs * 32 * P.nb > 65536) {
         set_error("grid of %d x %d nodes needs %zu bytes of shared memory in one CTA (limit %d)", P.nx, P.ny, P.smem,
                   optin);
         return EIK_EUNSUPPORTED;
@@ -174,9 +213,9 @@ static int fsm_run(const eik_grid *grid, const FsmPlan &P, const void *r, const 
         return rc;
     const size_t total = (size_t)P.nx * P.ny;
     const int tb = (int)std::min<size_t>((total + 255) / 256, (size_t)nsm * 16);
-    k_fsm_pack<T><<<tb, 256, 0, s>>>(A);
-    k_fsm_run<T><<<1, 32 * P.nb, P.smem, s>>>(A);
-    k_fsm_unpack<T><<<tb, 256, 0, s>>>(A, stats);
+    EIK_LAUNCH("fsm_pack", s, k_fsm_pack<T><<<tb, 256, 0, s>>>(A));
+    EIK_LAUNCH("fsm_sweeps", s, k_fsm_run<T><<<1, 32 * P.nb, P.smem, s>>>(A));
+    EIK_LAUNCH("fsm_unpack", s, k_fsm_unpack<T><<<tb, 256, 0, s>>>(A, stats));
     return cuda_check(cudaGetLastError(), "fsm launch");
 }
 
@@ -186,7 +225,37 @@ using namespace eik;
 
 extern "C" const char *eik_last_error(void) { return g_err; }
 
-extern "C" int eik_version(void) { return 100; }
+extern "C" int eik_version(void) { return 101; }
+
+extern "C" int eik_profile_enable(int on) {
+    int prev = g_prof_on ? 1 : 0;
+    g_prof_on = on != 0;
+    return prev;
+}
+
+extern "C" int eik_profile_collect(eik_kernel_time *out, int max_entries) {
+    std::vector<eik_kernel_time> acc;
+    int rc = EIK_OK;
+    for (auto &r : g_prof) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            set_error("eik_profile_collect: event query failed");
+            rc = EIK_ECUDA;
+        }
+        size_t k = 0;
+        while (k < acc.size() && std::string(acc[k].name) != r.name) ++k;
+        if (k == acc.size()) acc.push_back(eik_kernel_time{r.name, 0, 0.0, 0.0});
+        acc[k].launches += 1;
+        acc[k].total_ms += ms;
+        if (ms > acc[k].max_ms) acc[k].max_ms = ms;
+        g_prof_pool.push_back(r.a);
+        g_prof_pool.push_back(r.b);
+    }
+    g_prof.clear();
+    if (rc != EIK_OK) return rc;
+    for (size_t k = 0; k < acc.size() && (int)k < max_entries; ++k) out[k] = acc[k];
+    return (int)acc.size();
+}
 
 extern "C" size_t eik_fsm_workspace_size(const eik_grid *grid) {
     FsmPlan P;
@@ -202,8 +271,8 @@ extern "C" int eik_fsm(const eik_grid *grid, const void *r, const uint8_t *gamma
         set_error("eik_fsm: NULL array argument");
         return EIK_EINVAL;
     }
-    if (max_sweeps < 1) {
-        set_error("max_sweeps must be >= 1");
+    if (max_sweeps < 1 || max_sweeps > MAX_SWEEPS || grid->n[1] > MAX_BOX_ROWS) {
+        set_error("max_sweeps must be in [1, %lld] and n[1] <= %d", MAX_SWEEPS, MAX_BOX_ROWS);
         return EIK_EINVAL;
     }
     if (reinterpret_cast<uintptr_t>(ws) & 255) {

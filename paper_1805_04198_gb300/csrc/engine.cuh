@@ -6,22 +6,28 @@
 // Any schedule that respects exactly those four dependencies gives the same
 // result as the serial loop nest.  The schedule used here:
 //
-//  * the box is cut into 32-column blocks; one warp owns one block and one
-//    lane owns one column of it (logical column order follows the sweep sign
-//    of x, so lane 0 is the upwind side);
+//  * the box is cut into 32-column blocks; warp w owns physical block w for the
+//    whole run, lane l one column of it (lane order follows the sweep sign of
+//    x, so lane 0 is the upwind side);
 //  * at step s lane l updates logical row s - l: its left neighbour (new) comes
-//    from lane l-1 by a register shuffle, its upper neighbour (new) is the value
-//    it produced one step earlier, its right neighbour (old) is lane l+1's
-//    prefetched lower neighbour, shuffled down;
-//  * the block's rows stream through a 48-row shared-memory ring (6 chunks of
-//    8 rows): chunks are loaded two chunks ahead with coalesced 16-byte loads
-//    and written back as soon as all 32 lanes finished them;
-//  * lane 31 hands its new column to the next block's warp through shared
-//    memory, published every chunk; lane 31 reads the next block's first
-//    column (old values) from global memory, prefetched with the chunk;
-//  * per-node read-only data ("statics": slowness, masks, ...) are stored
-//    pre-skewed per sweep direction ([dir][block][step][lane]) so each step is
-//    one coalesced 128-byte load, prefetched a chunk ahead into registers.
+//    from lane l-1 by a register shuffle, its upper neighbour (new) is the
+//    value it produced one step earlier, its right neighbour (old) is lane
+//    l+1's prefetched lower neighbour, shuffled down;
+//  * the block's rows stream through a 64-row shared-memory ring in chunks of
+//    8 rows, copied from global memory by cp.async three chunks ahead and
+//    written back as soon as all 32 lanes finished them;
+//  * the block's last lane hands its new column to the next block's warp
+//    through shared memory (published per chunk, tagged with the sweep); it
+//    reads the next block's first column (old values) from global memory;
+//  * per-node read-only data ("statics") are stored pre-skewed per sweep
+//    direction ([dir][block][step][lane]) so a chunk of 8 steps is one
+//    contiguous copy into a small shared ring;
+//  * there is no CTA-wide barrier between sweeps: a warp starts sweep k+1 as
+//    soon as its own block and the block whose old column it reads have
+//    finished sweep k, so the pipeline reverses direction without draining
+//    when the x sign flips.  A sweep that changes no node anywhere marks a
+//    fixed point; the engine then stops (sweeps a warp had already begun
+//    speculatively change nothing).
 //
 // Storage of the state u: strip-major [block][row][32] (row = physical y,
 // 32 = physical x within the block), padded to a whole number of blocks;
@@ -33,9 +39,13 @@
 
 namespace eik {
 
-constexpr int CH = 8;            // rows per chunk
-constexpr int RS = 6;            // chunks held in the ring
-constexpr int RROWS = CH * RS;   // ring rows per warp
+constexpr int CH = 8;             // rows (and steps) per chunk
+constexpr int RROWS = 64;         // u ring rows per warp (power of two)
+constexpr int SRCH = 3;           // statics chunks held in the statics ring
+constexpr int LEAD = 3;           // u chunks copied ahead of the current one
+constexpr int SWEEP_SHIFT = 13;   // hand-off progress tag: rows < 2^13, sweeps < 2^18
+constexpr int MAX_BOX_ROWS = (1 << SWEEP_SHIFT) - 1;
+constexpr long long MAX_SWEEPS = 1ll << 17;
 
 __host__ __device__ inline int ceil32(int v) { return (v + 31) >> 5; }
 
@@ -44,7 +54,8 @@ __host__ __device__ inline size_t box_index(int i, int j, int my) {
     return ((size_t)(i >> 5) * my + j) * 32 + (i & 31);
 }
 
-__host__ __device__ inline int nstep_padded(int ny) { return ((ny + 31 + CH - 1) / CH) * CH + 2 * CH; }
+// Steps of one statics stream, padded to whole chunks plus the lead.
+__host__ __device__ inline int nstep_padded(int ny) { return ((ny + 31 + CH - 1) / CH) * CH + 4 * CH; }
 
 // Sweep direction d in [0, 4): bit 1 = sign of x, bit 0 = sign of y (set =
 // +1).  The paper's loop nest (x sign outermost, -1 first) visits d = 0..3 in
@@ -52,8 +63,9 @@ __host__ __device__ inline int nstep_padded(int ny) { return ((ny + 31 + CH - 1)
 __host__ __device__ inline int dir_sx(int d) { return (d & 2) ? 1 : -1; }
 __host__ __device__ inline int dir_sy(int d) { return (d & 1) ? 1 : -1; }
 
-// Index of node (i, j) of a box (width mx -> nb blocks, height my) in the
-// skewed statics layout for direction d.
+// Index of node (i, j) of a box (width -> nb blocks, height my) in the skewed
+// statics layout for direction d: [d][q][s][l], q = logical block, s = step,
+// l = lane.
 __host__ __device__ inline size_t skew_index(int d, int i, int j, int nb, int my, int nstepp) {
     int sx = dir_sx(d), sy = dir_sy(d);
     int b = i >> 5, pc = i & 31;
@@ -73,223 +85,317 @@ struct Box {
 };
 
 // Shared memory needed per CTA (one warp per block).
-template <class T>
+template <class T, int NST, bool HASB>
 __host__ __device__ inline size_t engine_smem_bytes(int nb, int ny) {
-    size_t per_warp = (size_t)RROWS * 32 * sizeof(T) + (size_t)RROWS * sizeof(T) +
-                      (size_t)((ny + 3) & ~3) * sizeof(T);
-    return nb * per_warp + 16 * sizeof(int) + (size_t)nb * sizeof(int) + 64;
+    size_t per_warp = (size_t)RROWS * 32 * sizeof(T)                 // u ring
+                      + (size_t)NST * SRCH * CH * 32 * sizeof(T)     // statics ring
+                      + (size_t)RROWS * sizeof(T)                    // halo ring
+                      + (size_t)((ny + 3) & ~3) * sizeof(T)          // hand-off column
+                      + (HASB ? (size_t)SRCH * CH * 32 : 0);         // byte statics ring
+    return nb * per_warp + (size_t)(32 + 2 * nb) * sizeof(int) + 64;
 }
 
-struct EngineShared {
-    int abort_flag;
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared control words of one engine run.
+struct EngineCtl {
+    int *prog;      // [nb] hand-off progress: (sweep << SWEEP_SHIFT) | rows published
+    int *done;      // [nb] sweeps completed by the block (all rows written back)
+    int *fin;       // [8] warps that finished sweep k (slot k & 7)
+    int *chg;       // [8] any node changed in sweep k
+    int *stop_at;   // first sweep that changed nothing (INT_MAX while unknown)
+    int *abort_flag;
 };
 
-template <class T>
-__device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
+__device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ void vstore(int *p, int v) { *(volatile int *)p = v; }
 
-// One sweep of one block by one warp.  Returns whether any node changed.
-template <class T, int NST, bool HASB, class P>
-__device__ bool run_block(const Box<T, NST> &bx, P &pol, int dir, int q, T *ring, T *halo, T *hand_out,
-                          const T *hand_in, volatile int *prog_out, volatile int *prog_in,
-                          volatile int *abort_flag, int *err) {
+// Bounded wait until *p >= target.  Returns false if the engine is stopping
+// (the last useful sweep is known to precede `sweep`) or on timeout.
+__device__ __forceinline__ bool wait_ge(const int *p, int target, const EngineCtl &C, int sweep, int *err) {
+    if (vload(p) >= target) return true;
+    long long it = 0;
+    while (vload(p) < target) {
+        if (vload(C.abort_flag) || vload(C.stop_at) < sweep) return false;
+        if (++it > SPIN_LIMIT) {
+            vstore(C.abort_flag, 1);
+            atomicExch(err, DEV_TIMEOUT);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+// One sweep (number k, direction (SX, SY)) of physical block b by its warp.
+// Returns -1 if the engine is stopping, else whether any node changed.
+template <int SX, int SY, class T, int NST, bool HASB, class P>
+__device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *ring, T *sring, uint8_t *sbring,
+                         T *halo, T *hand, const T *hands, size_t hand_elems, const EngineCtl &C, int *err) {
     using N = Num<T>;
+    constexpr int DIR = (SX > 0 ? 2 : 0) | (SY > 0 ? 1 : 0);
     const T INF = N::inf();
     const int lane = threadIdx.x & 31;
     const int NB = bx.nb, NY = bx.ny, NX = bx.nx;
-    const int sx = dir_sx(dir), sy = dir_sy(dir);
-    const int b = sx > 0 ? q : NB - 1 - q;
-    const int pc = sx > 0 ? lane : 31 - lane;
+    const int q = SX > 0 ? b : NB - 1 - b;         // logical block
+    const int pc = SX > 0 ? lane : 31 - lane;       // physical column in the block
     const int x = 32 * b + pc;
     const bool colok = x < NX;
-    const bool has_prev = q > 0;
-    const bool has_next = q + 1 < NB;
-    const int bn = sx > 0 ? b + 1 : b - 1;
-    const int pcn = sx > 0 ? 0 : 31;
+    const int bp = b - SX, bn = b + SX;              // physical predecessor / successor
+    const bool has_prev = bp >= 0 && bp < NB;
+    const bool has_next = bn >= 0 && bn < NB;
+    const int pcn = SX > 0 ? 0 : 31;                 // successor's first logical column
     const bool nextok = has_next && (32 * bn + pcn) < NX;
     T *ublk = bx.u + (size_t)b * NY * 32;
     const T *unext = bx.u + (size_t)(has_next ? bn : b) * NY * 32;
-    const size_t stbase = ((size_t)dir * NB + q) * bx.nstepp;
+    const T *hand_in = hands + (size_t)(has_prev ? bp : b) * hand_elems;
     const int nchunks = (NY + CH - 1) / CH;
     const int nsteps = NY + 31;
+    const int tag = k << SWEEP_SHIFT;
 
-    // staging: lane covers logical row r8 of the chunk, columns cg*8 .. cg*8+7
-    constexpr int SV = (8 * (int)sizeof(T)) / 16;
+    // Start condition: the successor block (whose old column this sweep reads)
+    // has finished sweep k-1.  Our own block finished it in program order.
+    if (k > 0 && has_next) {
+        if (!wait_ge(C.done + bn, k, C, k, err)) return -1;
+        __threadfence_block();
+    }
+
+    auto prow = [&](int m) { return SY > 0 ? m : NY - 1 - m; };
+    constexpr int EPL = 8;                                  // elements per lane per chunk
+    constexpr int CPL = EPL * (int)sizeof(T) / 16;          // 16-byte copies per lane
+    constexpr int E16 = 16 / (int)sizeof(T);                // elements per 16-byte copy
     const int r8 = lane >> 2, cg = lane & 3;
-    uint4 stage[SV];
-    T hstage = INF;
-
-    auto prow = [&](int m) { return sy > 0 ? m : NY - 1 - m; };
-    auto load_chunk = [&](int j) {
-        int m = j * CH + r8;
-        if (m < NY) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(ublk + (size_t)prow(m) * 32 + cg * 8);
+    auto issue_chunk = [&](int j) {                         // u rows of chunk j -> ring
+        const int m = j * CH + r8;
+        if (j < nchunks && m < NY) {
+            const T *src = ublk + (size_t)prow(m) * 32 + cg * EPL;
+            T *dst = ring + (m & (RROWS - 1)) * 32 + cg * EPL;
 #pragma unroll
-            for (int k = 0; k < SV; ++k) stage[k] = __ldcg(src + k);
+            for (int c = 0; c < CPL; ++c) cp_async16(dst + c * E16, src + c * E16);
         }
-        int mh = j * CH + lane;
-        hstage = INF;
-        if (lane < CH && nextok && mh < NY) hstage = ld_cg(unext + (size_t)prow(mh) * 32 + pcn);
     };
-    auto store_chunk = [&](int j) {
-        int m = j * CH + r8;
-        uint4 *dst = reinterpret_cast<uint4 *>(ring + ((j % RS) * CH + r8) * 32 + cg * 8);
-        if (m < NY) {
+    const size_t stbase = ((size_t)DIR * NB + q) * bx.nstepp;
+    auto issue_statics = [&](int j) {                       // statics of steps 8j.. -> statics ring
+        const int s0 = j * CH;
+        if (s0 + CH > bx.nstepp) return;
+        const int slot = j % SRCH;
 #pragma unroll
-            for (int k = 0; k < SV; ++k) dst[k] = stage[k];
+        for (int kk = 0; kk < NST; ++kk) {
+            const T *src = bx.st[kk] + (stbase + s0) * 32 + lane * EPL;
+            T *dst = sring + ((size_t)kk * SRCH * CH + slot * CH) * 32 + lane * EPL;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) cp_async16(dst + c * E16, src + c * E16);
         }
-        if (lane < CH) halo[(j % RS) * CH + lane] = hstage;
+        if (HASB && lane < 16) cp_async16(sbring + (slot * CH) * 32 + lane * 16, bx.sb + (stbase + s0) * 32 + lane * 16);
+    };
+    T hreg = INF;  // halo of one chunk (lanes 0..7), staged in a register
+    auto load_halo = [&](int j) {
+        const int mh = j * CH + lane;
+        hreg = (lane < CH && nextok && j < nchunks && mh < NY) ? __ldcg(unext + (size_t)prow(mh) * 32 + pcn) : INF;
     };
     auto write_back = [&](int j) {
-        int m = j * CH + r8;
+        const int m = j * CH + r8;
         if (m < NY) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(ring + ((j % RS) * CH + r8) * 32 + cg * 8);
-            uint4 *dst = reinterpret_cast<uint4 *>(ublk + (size_t)prow(m) * 32 + cg * 8);
+            const uint4 *src = reinterpret_cast<const uint4 *>(ring + (m & (RROWS - 1)) * 32 + cg * EPL);
+            uint4 *dst = reinterpret_cast<uint4 *>(ublk + (size_t)prow(m) * 32 + cg * EPL);
 #pragma unroll
-            for (int k = 0; k < SV; ++k) __stcg(dst + k, src[k]);
+            for (int c = 0; c < CPL; ++c) __stcg(dst + c, src[c]);
         }
     };
 
-    T stc[NST > 0 ? NST : 1][CH], stn[NST > 0 ? NST : 1][CH];
-    uint8_t sbc[CH], sbn[CH];
-    auto load_statics = [&](int j, T (&dst)[NST > 0 ? NST : 1][CH], uint8_t (&dsb)[CH]) {
+    // Prologue: u chunks 0..LEAD-1 and statics chunks 0..1 in flight (one
+    // group per chunk), halo of chunk 0 in the ring, of chunk 1 in hreg.
+    __threadfence_block();
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            int s = j * CH + i;
-            bool ok = s < bx.nstepp;
-            size_t idx = (stbase + (size_t)s) * 32 + lane;
-#pragma unroll
-            for (int k = 0; k < NST; ++k) dst[k][i] = ok ? __ldcg(bx.st[k] + idx) : T(0);
-            if (HASB) dsb[i] = ok ? __ldcg(bx.sb + idx) : (uint8_t)0;
-        }
-    };
+    for (int j = 0; j < LEAD; ++j) {
+        issue_chunk(j);
+        if (j < 2) issue_statics(j);
+        cp_async_commit();
+    }
+    load_halo(0);
+    if (lane < CH) halo[lane] = hreg;
+    load_halo(1);
 
-    // prologue: chunk 0 into the ring, chunk 1 staged, statics of chunks 0, 1
-    load_chunk(0);
-    store_chunk(0);
-    if (nchunks > 1) load_chunk(1);
-    load_statics(0, stc, sbc);
-    load_statics(1, stn, sbn);
-
-    T last = INF;
+    T last = INF, cur = INF, dnx = INF, hin = INF, hal = INF;
     bool changed = false;
-    const int lastJ = nchunks + RS - 2;  // boundary that writes back the last chunk
+    const int lastJ = nchunks + 4;                 // boundary that writes back the last chunk
+    const bool lane0 = lane == 0, lane31 = lane == 31;
+    T *myring = ring + pc;
+    int known = -1;
+    auto ringval = [&](int m) -> T {
+        return (colok && (unsigned)m < (unsigned)NY) ? myring[(m & (RROWS - 1)) * 32] : INF;
+    };
+    auto clampm = [&](int m) { return m < 0 ? 0 : (m >= NY ? NY - 1 : m); };
 
     for (int J = 0; J <= lastJ; ++J) {
         __syncwarp();
-        if (J >= RS - 1 && J - (RS - 1) < nchunks) write_back(J - (RS - 1));
-        if (has_next) {
-            // rows whose hand-off values lane 31 has written: m <= 8J - 32
-            int done = 8 * J - 31;
-            done = done < 0 ? 0 : (done > NY ? NY : done);
-            if (J == lastJ) done = NY;
-            if (lane == 31) {
-                __threadfence_block();
-                *prog_out = done;
-            }
+        // chunk J-5 is complete: its last row 8J-33 was updated by lane 31 at step 8J-2
+        if (J >= 5 && J - 5 < nchunks) write_back(J - 5);
+        if (has_next && lane31) {
+            int pub = CH * J - 31;  // rows whose hand-off values this lane has written
+            pub = pub < 0 ? 0 : (pub > NY ? NY : pub);
+            if (J == lastJ) pub = NY;
+            __threadfence_block();
+            vstore(C.prog + b, tag | pub);
         }
-        if (J + 1 < nchunks) store_chunk(J + 1);
-        if (J + 2 < nchunks) load_chunk(J + 2);
-        if (J > 0) {
-#pragma unroll
-            for (int i = 0; i < CH; ++i) {
-#pragma unroll
-                for (int k = 0; k < NST; ++k) stc[k][i] = stn[k][i];
-                if (HASB) sbc[i] = sbn[i];
-            }
-            load_statics(J + 1, stn, sbn);
-        }
+        // halo of chunk J+1 into the ring, load halo of chunk J+2
+        if (lane < CH) halo[((J + 1) * CH + lane) & (RROWS - 1)] = hreg;
+        load_halo(J + 2);
+        // copies for u chunk J+LEAD (into the slot of chunk J-5, written back
+        // above) and statics chunk J+2 (slot of chunk J-1, used up)
+        issue_chunk(J + LEAD);
+        issue_statics(J + 2);
+        cp_async_commit();
+        // the group of boundary J-2 (u chunk J+1, statics chunk J) has landed
+        cp_async_wait<2>();
         const int s0 = J * CH;
         if (s0 < nsteps && has_prev) {
-            int need = s0 + CH;
-            need = need > NY ? NY : need;
-            long long it = 0;
-            while (*prog_in < need) {
-                if (*abort_flag) break;
-                if (++it > SPIN_LIMIT) {
-                    *abort_flag = 1;
-                    atomicExch(err, DEV_TIMEOUT);
-                    break;
+            const int need = tag | (s0 + CH > NY ? NY : s0 + CH);
+            if (known < need) {
+                if (!wait_ge(C.prog + bp, need, C, k, err)) {
+                    cp_async_wait<0>();
+                    return -1;
                 }
-                __nanosleep(64);
+                known = vload(C.prog + bp);
+                __threadfence_block();
             }
-            __threadfence_block();
         }
         __syncwarp();
-        if (*abort_flag) break;
+        if ((J & 7) == 7 && (vload(C.abort_flag) || vload(C.stop_at) < k)) {
+            cp_async_wait<0>();
+            return -1;
+        }
         if (s0 >= nsteps) continue;
-
+        if (J == 0) {
+            cur = ringval(-lane);
+            dnx = ringval(1 - lane);
+        }
+        hin = hand_in[clampm(s0 - lane)];
+        hal = halo[(s0 - lane) & (RROWS - 1)];
+        const T *sbase = sring + (size_t)((J % SRCH) * CH) * 32 + lane;
+        const uint8_t *bbase = sbring + ((J % SRCH) * CH) * 32 + lane;
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
-            const int s = s0 + i;
-            const int m = s - lane;
+            const int m = s0 + i - lane;
             const bool rowok = (unsigned)m < (unsigned)NY;
-            const bool act = rowok && colok;
-            const int slot = rowok ? ((m >> 3) % RS) * CH + (m & 7) : 0;
-            T self = INF, dn = INF;
-            if (act) self = ring[slot * 32 + pc];
-            const int m1 = m + 1;
-            if (colok && (unsigned)m1 < (unsigned)NY) dn = ring[(((m1 >> 3) % RS) * CH + (m1 & 7)) * 32 + pc];
-            T left = __shfl_up_sync(FULL, last, 1);
-            T right = __shfl_down_sync(FULL, dn, 1);
-            if (lane == 0) left = (has_prev && rowok) ? hand_in[m] : INF;
-            if (lane == 31) right = (nextok && rowok) ? halo[slot] : INF;
-            const T up = last;
-            T nw = INF;
-            if (act) {
-                const T vmx = sx > 0 ? left : right, vpx = sx > 0 ? right : left;
-                const T vmy = sy > 0 ? up : dn, vpy = sy > 0 ? dn : up;
-                const int y = sy > 0 ? m : NY - 1 - m;
-                T sv[NST > 0 ? NST : 1];
+            const bool act = colok && rowok;
+            // loads for the next step, issued before this step's store
+            const T dn2 = ringval(m + 2);
+            const T hin2 = (i + 1 < CH) ? hand_in[clampm(m + 1)] : INF;
+            const T hal2 = halo[(m + 1) & (RROWS - 1)];
+            T sv[NST > 0 ? NST : 1];
 #pragma unroll
-                for (int k = 0; k < NST; ++k) sv[k] = stc[k][i];
-                nw = pol.update(self, vmx, vpx, vmy, vpy, sv, HASB ? sbc[i] : (uint8_t)0, x, y, changed);
-                ring[slot * 32 + pc] = nw;
-                if (lane == 31 && has_next) hand_out[m] = nw;
-            }
+            for (int kk = 0; kk < NST; ++kk) sv[kk] = sbase[((size_t)kk * SRCH * CH + i) * 32];
+            const uint8_t sbv = HASB ? bbase[i * 32] : (uint8_t)0;
+            const T fromleft = __shfl_up_sync(FULL, last, 1);
+            const T fromright = __shfl_down_sync(FULL, dnx, 1);
+            const T left = lane0 ? ((has_prev && rowok) ? hin : INF) : fromleft;
+            const T right = lane31 ? ((nextok && rowok) ? hal : INF) : fromright;
+            bool ch = false;
+            const T upd = pol.update(cur, SX > 0 ? left : right, SX > 0 ? right : left, SY > 0 ? last : dnx,
+                                     SY > 0 ? dnx : last, sv, sbv, ch);
+            const T nw = act ? upd : INF;
+            changed = changed || (act && ch);
+            if (act) myring[(m & (RROWS - 1)) * 32] = nw;
+            if (act && lane31 && has_next) hand[m] = nw;
             last = nw;
+            cur = dnx;
+            dnx = dn2;
+            hin = hin2;
+            hal = hal2;
         }
     }
-    return __any_sync(FULL, changed);
+    cp_async_wait<0>();
+    __threadfence_block();  // every lane's write-back before the block's completion flag
+    __syncwarp();
+    return __any_sync(FULL, changed) ? 1 : 0;
 }
 
 // Runs sweeps on one box until a sweep changes nothing or max_sweeps ran.
-// Requires blockDim.x == 32 * bx.nb and engine_smem_bytes<T>(nb, ny) bytes of
-// dynamic shared memory starting at `smem`.  All threads must call it.
+// Requires blockDim.x >= 32 * bx.nb and engine_smem_bytes<T, NST, HASB>(nb, ny)
+// bytes of dynamic shared memory at `smem`.  All threads must call it.
 template <class T, int NST, bool HASB, class P>
-__device__ void engine_run(const Box<T, NST> &bx, P &pol, long long max_sweeps, char *smem, long long &sweeps,
+__device__ void engine_run(const Box<T, NST> &bx, const P &pol, long long max_sweeps, char *smem, long long &sweeps,
                            bool &converged, int *err) {
     const int nw = bx.nb;
     const int warp = threadIdx.x >> 5;
-    const size_t ring_elems = (size_t)RROWS * 32, halo_elems = RROWS, hand_elems = (size_t)((bx.ny + 3) & ~3);
+    const int lane = threadIdx.x & 31;
+    const size_t ring_e = (size_t)RROWS * 32, sring_e = (size_t)NST * SRCH * CH * 32;
+    const size_t halo_e = RROWS, hand_e = (size_t)((bx.ny + 3) & ~3);
+    const size_t sb_b = HASB ? (size_t)SRCH * CH * 32 : 0;
     T *base = reinterpret_cast<T *>(smem);
-    T *ring = base + (size_t)warp * ring_elems;
-    T *halo = base + (size_t)nw * ring_elems + (size_t)warp * halo_elems;
-    T *hands = base + (size_t)nw * (ring_elems + halo_elems);
-    int *ints = reinterpret_cast<int *>(hands + (size_t)nw * hand_elems);
-    volatile int *abort_flag = ints;
-    volatile int *prog = ints + 16;
+    T *ring = base + (size_t)warp * ring_e;
+    T *sring = base + (size_t)nw * ring_e + (size_t)warp * sring_e;
+    T *halo = base + (size_t)nw * (ring_e + sring_e) + (size_t)warp * halo_e;
+    T *hands = base + (size_t)nw * (ring_e + sring_e + halo_e);
+    uint8_t *bytes = reinterpret_cast<uint8_t *>(hands + (size_t)nw * hand_e);
+    uint8_t *sbring = bytes + (size_t)warp * sb_b;
+    int *ints = reinterpret_cast<int *>(bytes + (size_t)nw * sb_b);
+    EngineCtl C;
+    C.abort_flag = ints;
+    C.stop_at = ints + 1;
+    C.fin = ints + 8;
+    C.chg = ints + 16;
+    C.prog = ints + 32;
+    C.done = ints + 32 + nw;
 
-    if (threadIdx.x == 0) *abort_flag = 0;
-    sweeps = 0;
-    converged = false;
-    while (sweeps < max_sweeps) {
-        const int dir = (int)(sweeps & 3);
-        if ((int)threadIdx.x < nw) prog[threadIdx.x] = 0;
-        __syncthreads();
-        bool ch = false;
-        if (warp < nw) {
-            ch = run_block<T, NST, HASB>(bx, pol, dir, warp, ring, halo, hands + (size_t)warp * hand_elems,
-                                         hands + (size_t)(warp > 0 ? warp - 1 : 0) * hand_elems, prog + warp,
-                                         prog + (warp > 0 ? warp - 1 : 0), abort_flag, err);
-        }
-        const int any = __syncthreads_or(ch ? 1 : 0);
-        ++sweeps;
-        if (*abort_flag) break;
-        if (!any) {
-            converged = true;
-            break;
+    if (threadIdx.x == 0) {
+        C.abort_flag[0] = 0;
+        C.stop_at[0] = 0x7fffffff;
+    }
+    if (threadIdx.x < 8) {
+        C.fin[threadIdx.x] = 0;
+        C.chg[threadIdx.x] = 0;
+    }
+    if ((int)threadIdx.x < nw) {
+        C.prog[threadIdx.x] = -1;
+        C.done[threadIdx.x] = 0;
+    }
+    __syncthreads();
+
+    if (warp < nw) {
+        const int b = warp;
+        T *hand = hands + (size_t)b * hand_e;
+        for (long long kk = 0; kk < max_sweeps; ++kk) {
+            const int k = (int)kk;
+            if (vload(C.abort_flag) || vload(C.stop_at) < k) break;
+            int ch;
+            switch (k & 3) {
+                case 0: ch = run_block<-1, -1, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                case 1: ch = run_block<-1, +1, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                case 2: ch = run_block<+1, -1, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                default: ch = run_block<+1, +1, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+            }
+            if (ch < 0) break;
+            // sweep k of this block is complete: publish it, then the sweep status
+            if (lane == 0) {
+                __threadfence_block();
+                vstore(C.done + b, k + 1);
+                if (ch) atomicOr(C.chg + (k & 7), 1);
+                __threadfence_block();
+                const int f = atomicAdd(C.fin + (k & 7), 1);
+                if (f == nw - 1) {
+                    if (vload(C.chg + (k & 7)) == 0) {
+                        atomicMin(C.stop_at, k);
+                    } else {
+                        vstore(C.chg + (k & 7), 0);
+                        vstore(C.fin + (k & 7), 0);
+                    }
+                }
+            }
+            __syncwarp();
         }
     }
+    __syncthreads();
+    const int st = vload(C.stop_at);
+    converged = st != 0x7fffffff && !vload(C.abort_flag);
+    sweeps = st != 0x7fffffff ? (long long)st + 1 : max_sweeps;
     __syncthreads();
 }
 

@@ -9,7 +9,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/eik.h"
+#include "eik.h"
 
 namespace eik {
 

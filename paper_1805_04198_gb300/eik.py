@@ -40,7 +40,8 @@ class Grid(ctypes.Structure):
 
 
 class FsmStats(ctypes.Structure):
-    _fields_ = [("sweeps", ctypes.c_int64), ("converged", ctypes.c_int), ("error", ctypes.c_int)]
+    _fields_ = [("sweeps", ctypes.c_int64), ("converged", ctypes.c_int), ("error", ctypes.c_int),
+                ("updates", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
 class DDParams(ctypes.Structure):
@@ -53,7 +54,13 @@ class DDStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("error", ctypes.c_int),
                 ("causal_rounds_max", ctypes.c_int), ("fsm_sweeps_max", ctypes.c_int64),
                 ("coarse_sweeps_max", ctypes.c_int64), ("fsm_cap_hits", ctypes.c_int64),
-                ("coarse_cap_hits", ctypes.c_int64), ("last_delta", ctypes.c_double)]
+                ("coarse_cap_hits", ctypes.c_int64), ("last_delta", ctypes.c_double),
+                ("fine_updates", ctypes.c_int64), ("coarse_updates", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double)]
 
 
 def _as_dict(s):
@@ -81,6 +88,10 @@ def load():
         lib.eik_dd_solve.restype = ctypes.c_int
         lib.eik_dd_solve.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp,
                                      ctypes.c_size_t, vp, vp]
+        lib.eik_profile_enable.restype = ctypes.c_int
+        lib.eik_profile_enable.argtypes = [ctypes.c_int]
+        lib.eik_profile_collect.restype = ctypes.c_int
+        lib.eik_profile_collect.argtypes = [ctypes.POINTER(KernelTime), ctypes.c_int]
         _lib = lib
         return lib
 
@@ -137,6 +148,22 @@ def _workspace(nbytes, device):
 def _aligned(ws):
     off = (-ws.data_ptr()) % 256
     return ctypes.c_void_p(ws.data_ptr() + off), ws.numel() - off
+
+
+def eik_profile_enable(on: bool) -> bool:
+    return bool(load().eik_profile_enable(1 if on else 0))
+
+
+def eik_profile_collect() -> dict:
+    """{kernel name: {launches, total_ms, max_ms}} of the launches timed since
+    the last collect (waits for their events)."""
+    lib = load()
+    buf = (KernelTime * 64)()
+    n = lib.eik_profile_collect(buf, 64)
+    if n < 0:
+        raise EikError(n, eik_last_error())
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
+                                   "max_ms": buf[i].max_ms} for i in range(min(n, 64))}
 
 
 def eik_fsm_workspace_size(grid: Grid) -> int:
