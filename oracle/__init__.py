@@ -53,7 +53,8 @@ class DDStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("last_delta", ctypes.c_double),
                 ("fsm_sweeps_max", ctypes.c_long), ("coarse_sweeps_max", ctypes.c_long),
                 ("fsm_cap_hits", ctypes.c_long), ("coarse_cap_hits", ctypes.c_long),
-                ("causal_rounds_max", ctypes.c_long)]
+                ("causal_rounds_max", ctypes.c_long), ("fine_updates", ctypes.c_longlong),
+                ("coarse_updates", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

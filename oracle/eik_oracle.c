@@ -803,6 +803,11 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
             first = 0;
             s = step1_grid(&G, o, H, r, gamma, g, U, W, p->max_coarse_sweeps, &S0.coarse_cap_hits);
             if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
+            {
+                long m[3];
+                grid_box(&G, o, m);
+                S0.coarse_updates += (long long)s * m[0] * m[1] * m[2];
+            }
         }
     }
     {
@@ -823,6 +828,7 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
                     long s = step23_tile(&G, t, p->h, r, gamma, g, U, W, tu[ti], tw[ti], p->max_fsm_sweeps,
                                          &S0.fsm_cap_hits);
                     if (s > S0.fsm_sweeps_max) S0.fsm_sweeps_max = s;
+                    S0.fine_updates += (long long)s * tilenodes;
                     ++ti;
                 }
         /* Alg. 4 */
@@ -846,6 +852,11 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
                 s = step4_grid(&G, o, H, p->theta, r, gamma, g, Uprev, uk, wk, W, Unew, p->max_coarse_sweeps,
                                &S0.coarse_cap_hits);
                 if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
+                {
+                    long m[3];
+                    grid_box(&G, o, m);
+                    S0.coarse_updates += (long long)s * m[0] * m[1] * m[2];
+                }
             }
             memcpy(U, Unew, sizeof(double) * (size_t)G.N);
             free(Unew);

@@ -63,6 +63,8 @@ typedef struct {
     long fsm_cap_hits;    /* fine solves stopped by max_fsm_sweeps */
     long coarse_cap_hits; /* coarse solves stopped by max_coarse_sweeps */
     long causal_rounds_max; /* rounds of 2^d causal passes until no change (>=1) */
+    long long fine_updates;   /* local solves executed in subdomain sweeps */
+    long long coarse_updates; /* local solves executed in coarse-grid sweeps */
 } orc_dd_stats;
 
 /* The two-scale DD / theta-parareal iteration of Sec. 3 (Steps 1-4, Alg. 1-5),
