@@ -140,6 +140,29 @@ int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, cons
                  const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes,
                  eik_dd_stats *stats, void *stream);
 
+/*
+ * eik_dd_solve_noalloc: eik_dd_solve for callers that cannot allocate device
+ * memory (for example while a CUDA graph is being captured, or when another
+ * runtime owns the allocator).  It takes no workspace: the scratch is a static
+ * device array of EIK_NOALLOC_SCRATCH_BYTES inside the library, which every
+ * GPU that loads the library keeps until the process exits.  This entry point
+ * has no counterpart in the paper; it only changes where the scratch lives.
+ *  - Problems whose eik_dd_workspace_size exceeds the array are rejected with
+ *    EIK_ENOMEM before any work is enqueued.
+ *  - The first call on a device looks up the array's device address (a
+ *    cudaGetSymbolAddress call, made once per device with that device
+ *    current); make that first call before any stream capture.
+ *  - It calls no cudaMalloc/cudaFree or other allocating routine.
+ *  - All calls share the one array: calls whose work overlaps on the GPU
+ *    (different streams, or different host threads) race and must be
+ *    serialised by the caller.  The array keeps the last call's contents; the
+ *    solve needs no cleared scratch.
+ * Arguments and results are those of eik_dd_solve.
+ */
+#define EIK_NOALLOC_SCRATCH_BYTES (32u << 20)
+int eik_dd_solve_noalloc(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                         const eik_dd_params *params, void *u_out, eik_dd_stats *stats, void *stream);
+
 /* ------------------------------------------------------------------------- */
 /* Optional per-kernel timing (a benchmarking aid, off by default).  While     */
 /* enabled, every kernel the library launches is bracketed by two CUDA events  */

@@ -910,3 +910,65 @@ extern "C" int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *
     if (grid->dtype == EIK_F64) return dd_run<double>(grid, r, gamma, g, params, u_out, ws, stats, s);
     return dd_run<float>(grid, r, gamma, g, params, u_out, ws, stats, s);
 }
+
+// --------------------------------------------------------------------------
+// Entry point that allocates nothing: the DD workspace lives in a file-scope
+// device array instead of caller memory.
+//
+// Some callers cannot call cudaMalloc at all: code running inside a CUDA graph
+// that is being captured (allocation calls are not capturable), hosts whose
+// allocator is owned by another runtime that must not be bypassed, and
+// real-time loops that forbid allocation after start-up.  For them the scratch
+// is a static __device__ array of EIK_NOALLOC_SCRATCH_BYTES (32 MiB), which
+// every GPU that loads this library keeps until the process exits.
+// --------------------------------------------------------------------------
+#include <mutex>
+
+namespace eik {
+
+static __device__ __align__(256) unsigned char g_dd_scratch[EIK_NOALLOC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+static void *g_scratch_ptr[MAX_DEVICES];
+static std::mutex g_scratch_mu;
+
+// Device address of g_dd_scratch on the current device, looked up once per
+// device (the host-side name of the array is only a stand-in for it).
+static int scratch_address(void **out) {
+    int dev = 0;
+    int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    if (dev < 0 || dev >= MAX_DEVICES) {
+        set_error("device index %d beyond the %d devices this entry point supports", dev, MAX_DEVICES);
+        return EIK_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        rc = cuda_check(cudaGetSymbolAddress(&p, g_dd_scratch), "cudaGetSymbolAddress(scratch)");
+        if (rc) return rc;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return EIK_OK;
+}
+
+}  // namespace eik
+
+extern "C" int eik_dd_solve_noalloc(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                                    const eik_dd_params *params, void *u_out, eik_dd_stats *stats, void *stream) {
+    const size_t need = eik_dd_workspace_size(grid, params);
+    if (need == 0) return EIK_EINVAL;
+    if (need > (size_t)EIK_NOALLOC_SCRATCH_BYTES) {
+        set_error("eik_dd_solve_noalloc: problem needs %zu bytes of scratch, the static scratch holds %zu; "
+                  "use eik_dd_solve with a caller workspace",
+                  need, (size_t)EIK_NOALLOC_SCRATCH_BYTES);
+        return EIK_ENOMEM;
+    }
+    void *ws = nullptr;
+    const int rc = scratch_address(&ws);
+    if (rc) return rc;
+    // The workspace needs no clearing: every word the solve reads is written
+    // earlier in the same solve (the statistics and control words included).
+    return eik_dd_solve(grid, r, gamma, g, params, u_out, ws, (size_t)EIK_NOALLOC_SCRATCH_BYTES, stats, stream);
+}

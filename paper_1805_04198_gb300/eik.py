@@ -88,6 +88,8 @@ def load():
         lib.eik_dd_solve.restype = ctypes.c_int
         lib.eik_dd_solve.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp,
                                      ctypes.c_size_t, vp, vp]
+        lib.eik_dd_solve_noalloc.restype = ctypes.c_int
+        lib.eik_dd_solve_noalloc.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp, vp]
         lib.eik_profile_enable.restype = ctypes.c_int
         lib.eik_profile_enable.argtypes = [ctypes.c_int]
         lib.eik_profile_collect.restype = ctypes.c_int
@@ -187,6 +189,17 @@ def eik_dd_solve(grid, r, gamma, g, params, u_out, ws, stats_dev, stream=None):
     wsp, wsn = _aligned(ws)
     _check(lib.eik_dd_solve(ctypes.byref(grid), _ptr(r), _ptr(gamma), _ptr(g), ctypes.byref(params), _ptr(u_out),
                             wsp, wsn, _ptr(stats_dev), _stream(stream)))
+
+
+def eik_dd_solve_noalloc(grid, r, gamma, g, params, u_out, stats_dev, stream=None):
+    """eik_dd_solve with the library's static scratch instead of a workspace
+    (for callers that cannot allocate device memory)."""
+    lib = load()
+    _check(lib.eik_dd_solve_noalloc(ctypes.byref(grid), _ptr(r), _ptr(gamma), _ptr(g), ctypes.byref(params),
+                                    _ptr(u_out), _ptr(stats_dev), _stream(stream)))
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def dd_params(tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
