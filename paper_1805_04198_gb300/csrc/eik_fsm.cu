@@ -77,9 +77,12 @@ struct FsmArgs {
     int nx, ny, nb, nstepp;
     T *state;
     T *rsk;
+    T *ghands;   // multi-CTA hand-off columns [nb][ny]
+    int *gctl;   // multi-CTA control words
     FsmDev *dev;
     T h;
     long long max_sweeps;
+    int launches;
 };
 
 template <class T>
@@ -132,6 +135,35 @@ __global__ void k_fsm_run(FsmArgs<T> A) {
     }
 }
 
+// Multi-CTA form for grids wider than one CTA's blocks: cooperative launch,
+// hand-offs and control words in global memory.
+template <class T>
+__global__ void k_fsm_init_global(FsmArgs<T> A) {
+    engine_global_init(A.gctl, A.nb);
+    if (threadIdx.x == 0) A.dev->err = 0;
+}
+
+template <class T>
+__global__ void k_fsm_run_global(FsmArgs<T> A) {
+    extern __shared__ __align__(16) char smem[];
+    Box<T, 1> bx;
+    bx.u = A.state;
+    bx.st[0] = A.rsk;
+    bx.sb = nullptr;
+    bx.nx = A.nx;
+    bx.ny = A.ny;
+    bx.nb = A.nb;
+    bx.nstepp = A.nstepp;
+    PlainFsmPolicy<T> pol{A.h};
+    long long sweeps;
+    bool conv;
+    engine_run<T, 1, false, true>(bx, pol, A.max_sweeps, smem, sweeps, conv, &A.dev->err, A.ghands, A.gctl);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.dev->sweeps = (unsigned long long)sweeps;
+        A.dev->converged = conv ? 1 : 0;
+    }
+}
+
 template <class T>
 __global__ void k_fsm_unpack(FsmArgs<T> A, eik_fsm_stats *out) {
     const size_t total = (size_t)A.nx * A.ny;
@@ -144,13 +176,15 @@ __global__ void k_fsm_unpack(FsmArgs<T> A, eik_fsm_stats *out) {
         out->converged = A.dev->converged;
         out->error = A.dev->err;
         out->updates = (int64_t)A.dev->sweeps * A.nx * A.ny;
-        out->launches = 3;
+        out->launches = A.launches;
     }
 }
 
 struct FsmPlan {
     int nx, ny, nb, nstepp;
     size_t smem, bytes;
+    size_t gsmem;  // multi-CTA shared memory per CTA
+    int wpc;       // multi-CTA warps (blocks) per CTA
 };
 
 template <class T>
@@ -158,10 +192,14 @@ static size_t fsm_layout(const FsmPlan &P, FsmArgs<T> *A, void *ws) {
     Carver cv(ws);
     T *state = cv.take<T>((size_t)P.nb * P.ny * 32);
     T *rsk = cv.take<T>((size_t)4 * P.nb * P.nstepp * 32);
+    T *ghands = cv.take<T>((size_t)P.nb * P.ny);
+    int *gctl = cv.take<int>(engine_global_ints(P.nb));
     FsmDev *dev = cv.take<FsmDev>(1);
     if (A) {
         A->state = state;
         A->rsk = rsk;
+        A->ghands = ghands;
+        A->gctl = gctl;
         A->dev = dev;
     }
     return cv.used + 256;
@@ -175,6 +213,9 @@ static bool fsm_plan(const eik_grid *grid, FsmPlan &P) {
     P.nstepp = nstep_padded(P.ny);
     P.smem = grid->dtype == EIK_F64 ? engine_smem_bytes<double, 1, false>(P.nb, P.ny)
                                      : engine_smem_bytes<float, 1, false>(P.nb, P.ny);
+    P.wpc = 2;
+    P.gsmem = grid->dtype == EIK_F64 ? engine_smem_bytes<double, 1, false, true>(P.wpc, P.ny)
+                                      : engine_smem_bytes<float, 1, false, true>(P.wpc, P.ny);
     P.bytes = grid->dtype == EIK_F64 ? fsm_layout<double>(P, nullptr, nullptr) : fsm_layout<float>(P, nullptr, nullptr);
     return true;
 }
@@ -196,6 +237,7 @@ static int fsm_run(const eik_grid *grid, const FsmPlan &P, const void *r, const 
     A.h = (T)grid->h;
     A.max_sweeps = max_sweeps;
     fsm_layout<T>(P, &A, ws);
+    A.launches = 3;
     int rc;
     int dev, optin = 0, nsm = 0;
     if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
@@ -203,18 +245,39 @@ static int fsm_run(const eik_grid *grid, const FsmPlan &P, const void *r, const 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncAttributes fa;
     if ((rc = cuda_check(cudaFuncGetAttributes(&fa, k_fsm_run<T>), "func attr"))) return rc;
-    if ((int)P.smem > optin || P.nb > 32 || (long long)fa.numRegs * 32 * P.nb > 65536) {
-        set_error("grid of %d x %d nodes needs %zu bytes of shared memory in one CTA (limit %d)", P.nx, P.ny, P.smem,
-                  optin);
-        return EIK_EUNSUPPORTED;
-    }
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_fsm_run<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem),
-                         "smem attr")))
-        return rc;
+    const bool single = (int)P.smem <= optin && P.nb <= 32 && (long long)fa.numRegs * 32 * P.nb <= 65536;
+    A.launches = single ? 3 : 4;
     const size_t total = (size_t)P.nx * P.ny;
     const int tb = (int)std::min<size_t>((total + 255) / 256, (size_t)nsm * 16);
     EIK_LAUNCH("fsm_pack", s, k_fsm_pack<T><<<tb, 256, 0, s>>>(A));
-    EIK_LAUNCH("fsm_sweeps", s, k_fsm_run<T><<<1, 32 * P.nb, P.smem, s>>>(A));
+    if (single) {
+        if ((rc = cuda_check(cudaFuncSetAttribute(k_fsm_run<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)P.smem), "smem attr")))
+            return rc;
+        EIK_LAUNCH("fsm_sweeps", s, k_fsm_run<T><<<1, 32 * P.nb, P.smem, s>>>(A));
+    } else {
+        // one CTA per P.wpc blocks, all co-resident
+        const int nblk = (P.nb + P.wpc - 1) / P.wpc;
+        if ((rc = cuda_check(cudaFuncSetAttribute(k_fsm_run_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)P.gsmem), "smem attr")))
+            return rc;
+        int per_sm = 0;
+        if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsm_run_global<T>, 32 * P.wpc,
+                                                                          P.gsmem), "occupancy")))
+            return rc;
+        if (per_sm * nsm < nblk) {
+            set_error("grid of %d x %d nodes needs %d co-resident CTAs, the device holds %d", P.nx, P.ny, nblk,
+                      per_sm * nsm);
+            return EIK_EUNSUPPORTED;
+        }
+        EIK_LAUNCH("fsm_init", s, k_fsm_init_global<T><<<1, 256, 0, s>>>(A));
+        void *args[] = {&A};
+        int tok = prof_begin("fsm_sweeps", s);
+        rc = cuda_check(cudaLaunchCooperativeKernel((void *)k_fsm_run_global<T>, nblk, 32 * P.wpc, args, P.gsmem, s),
+                        "fsm cooperative launch");
+        prof_end(tok, s);
+        if (rc) return rc;
+    }
     EIK_LAUNCH("fsm_unpack", s, k_fsm_unpack<T><<<tb, 256, 0, s>>>(A, stats));
     return cuda_check(cudaGetLastError(), "fsm launch");
 }

@@ -84,16 +84,22 @@ struct Box {
     int nx, ny, nb, nstepp;
 };
 
-// Shared memory needed per CTA (one warp per block).
-template <class T, int NST, bool HASB>
-__host__ __device__ inline size_t engine_smem_bytes(int nb, int ny) {
+// Shared memory needed per CTA of `nw` warps (one warp per block).  With
+// GLOBAL the hand-off columns and control words live in global memory.
+template <class T, int NST, bool HASB, bool GLOBAL = false>
+__host__ __device__ inline size_t engine_smem_bytes(int nw, int ny) {
     size_t per_warp = (size_t)RROWS * 32 * sizeof(T)                 // u ring
                       + (size_t)NST * SRCH * CH * 32 * sizeof(T)     // statics ring
                       + (size_t)RROWS * sizeof(T)                    // halo ring
-                      + (size_t)((ny + 3) & ~3) * sizeof(T)          // hand-off column
+                      + (GLOBAL ? 0 : (size_t)((ny + 3) & ~3) * sizeof(T))  // hand-off column
                       + (HASB ? (size_t)SRCH * CH * 32 : 0);         // byte statics ring
-    return nb * per_warp + (size_t)(32 + 2 * nb) * sizeof(int) + 64;
+    return nw * per_warp + (GLOBAL ? 0 : (size_t)(32 + 2 * nw) * sizeof(int)) + 64;
 }
+
+// Control words of a multi-CTA engine run (global memory, zeroed by
+// engine_global_init before the run): abort, stop_at, fin[8], chg[8], then
+// prog[nb], done[nb].
+__host__ __device__ inline size_t engine_global_ints(int nb) { return 32 + 2 * (size_t)nb; }
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -115,6 +121,11 @@ struct EngineCtl {
 
 __device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
 __device__ __forceinline__ void vstore(int *p, int v) { *(volatile int *)p = v; }
+template <bool GLOBAL>
+__device__ __forceinline__ void fence() {
+    if (GLOBAL) __threadfence();
+    else __threadfence_block();
+}
 
 // Bounded wait until *p >= target.  Returns false if the engine is stopping
 // (the last useful sweep is known to precede `sweep`) or on timeout.
@@ -135,7 +146,7 @@ __device__ __forceinline__ bool wait_ge(const int *p, int target, const EngineCt
 
 // One sweep (number k, direction (SX, SY)) of physical block b by its warp.
 // Returns -1 if the engine is stopping, else whether any node changed.
-template <int SX, int SY, class T, int NST, bool HASB, class P>
+template <int SX, int SY, bool GLOBAL, class T, int NST, bool HASB, class P>
 __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *ring, T *sring, uint8_t *sbring,
                          T *halo, T *hand, const T *hands, size_t hand_elems, const EngineCtl &C, int *err) {
     using N = Num<T>;
@@ -163,7 +174,7 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
     // has finished sweep k-1.  Our own block finished it in program order.
     if (k > 0 && has_next) {
         if (!wait_ge(C.done + bn, k, C, k, err)) return -1;
-        __threadfence_block();
+        fence<GLOBAL>();
     }
 
     auto prow = [&](int m) { return SY > 0 ? m : NY - 1 - m; };
@@ -211,7 +222,7 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
 
     // Prologue: u chunks 0..LEAD-1 and statics chunks 0..1 in flight (one
     // group per chunk), halo of chunk 0 in the ring, of chunk 1 in hreg.
-    __threadfence_block();
+    fence<GLOBAL>();
 #pragma unroll
     for (int j = 0; j < LEAD; ++j) {
         issue_chunk(j);
@@ -222,16 +233,30 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
     if (lane < CH) halo[lane] = hreg;
     load_halo(1);
 
-    T last = INF, cur = INF, dnx = INF, hin = INF, hal = INF;
+    T last = INF, cur = INF, dnx = INF, hal = INF;
+    // hand-off values of the current chunk: lane i holds logical row s0 + i;
+    // with GLOBAL the next chunk's values are fetched one boundary ahead
+    T hcur = INF, hnext = INF;
+    auto hand_row = [&](int m) -> T {
+        return (lane < CH && m < NY) ? (GLOBAL ? __ldcg(hand_in + m) : hand_in[m]) : INF;
+    };
     bool changed = false;
     const int lastJ = nchunks + 4;                 // boundary that writes back the last chunk
     const bool lane0 = lane == 0, lane31 = lane == 31;
     T *myring = ring + pc;
     int known = -1;
+    if (GLOBAL && has_prev) {
+        if (!wait_ge(C.prog + bp, tag | (CH > NY ? NY : CH), C, k, err)) {
+            cp_async_wait<0>();
+            return -1;
+        }
+        known = vload(C.prog + bp);
+        fence<GLOBAL>();
+        hnext = hand_row(lane);
+    }
     auto ringval = [&](int m) -> T {
         return (colok && (unsigned)m < (unsigned)NY) ? myring[(m & (RROWS - 1)) * 32] : INF;
     };
-    auto clampm = [&](int m) { return m < 0 ? 0 : (m >= NY ? NY - 1 : m); };
 
     for (int J = 0; J <= lastJ; ++J) {
         __syncwarp();
@@ -241,7 +266,7 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
             int pub = CH * J - 31;  // rows whose hand-off values this lane has written
             pub = pub < 0 ? 0 : (pub > NY ? NY : pub);
             if (J == lastJ) pub = NY;
-            __threadfence_block();
+            fence<GLOBAL>();
             vstore(C.prog + b, tag | pub);
         }
         // halo of chunk J+1 into the ring, load halo of chunk J+2
@@ -256,14 +281,23 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
         cp_async_wait<2>();
         const int s0 = J * CH;
         if (s0 < nsteps && has_prev) {
-            const int need = tag | (s0 + CH > NY ? NY : s0 + CH);
+            // rows this chunk needs (smem hand-off) or the next chunk needs
+            // (global hand-off, fetched a boundary ahead)
+            const int rows = GLOBAL ? s0 + 2 * CH : s0 + CH;
+            const int need = tag | (rows > NY ? NY : rows);
             if (known < need) {
                 if (!wait_ge(C.prog + bp, need, C, k, err)) {
                     cp_async_wait<0>();
                     return -1;
                 }
                 known = vload(C.prog + bp);
-                __threadfence_block();
+                fence<GLOBAL>();
+            }
+            if (GLOBAL) {
+                hcur = hnext;
+                hnext = hand_row(s0 + CH + lane);
+            } else {
+                hcur = hand_row(s0 + lane);
             }
         }
         __syncwarp();
@@ -276,7 +310,6 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
             cur = ringval(-lane);
             dnx = ringval(1 - lane);
         }
-        hin = hand_in[clampm(s0 - lane)];
         hal = halo[(s0 - lane) & (RROWS - 1)];
         const T *sbase = sring + (size_t)((J % SRCH) * CH) * 32 + lane;
         const uint8_t *bbase = sbring + ((J % SRCH) * CH) * 32 + lane;
@@ -287,12 +320,12 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
             const bool act = colok && rowok;
             // loads for the next step, issued before this step's store
             const T dn2 = ringval(m + 2);
-            const T hin2 = (i + 1 < CH) ? hand_in[clampm(m + 1)] : INF;
             const T hal2 = halo[(m + 1) & (RROWS - 1)];
             T sv[NST > 0 ? NST : 1];
 #pragma unroll
             for (int kk = 0; kk < NST; ++kk) sv[kk] = sbase[((size_t)kk * SRCH * CH + i) * 32];
             const uint8_t sbv = HASB ? bbase[i * 32] : (uint8_t)0;
+            const T hin = __shfl_sync(FULL, hcur, i);
             const T fromleft = __shfl_up_sync(FULL, last, 1);
             const T fromright = __shfl_down_sync(FULL, dnx, 1);
             const T left = lane0 ? ((has_prev && rowok) ? hin : INF) : fromleft;
@@ -307,80 +340,94 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
             last = nw;
             cur = dnx;
             dnx = dn2;
-            hin = hin2;
             hal = hal2;
         }
     }
     cp_async_wait<0>();
-    __threadfence_block();  // every lane's write-back before the block's completion flag
+    fence<GLOBAL>();  // every lane's write-back before the block's completion flag
     __syncwarp();
     return __any_sync(FULL, changed) ? 1 : 0;
 }
 
 // Runs sweeps on one box until a sweep changes nothing or max_sweeps ran.
-// Requires blockDim.x >= 32 * bx.nb and engine_smem_bytes<T, NST, HASB>(nb, ny)
-// bytes of dynamic shared memory at `smem`.  All threads must call it.
-template <class T, int NST, bool HASB, class P>
+// Single-CTA form (GLOBAL = false): the CTA holds every block of the box,
+// blockDim.x >= 32 * bx.nb, engine_smem_bytes<T, NST, HASB>(nb, ny) bytes of
+// dynamic shared memory at `smem`.  Multi-CTA form (GLOBAL = true): CTA c
+// owns blocks [c * nw, c * nw + nw) with nw = blockDim.x / 32, hand-off
+// columns live in `ghands` ([nb][ny] elements) and the control words in
+// `gctl` (engine_global_ints(nb) ints, zeroed before the launch); every CTA of
+// the grid must be co-resident (cooperative launch).  All threads must call it.
+template <class T, int NST, bool HASB, bool GLOBAL = false, class P>
 __device__ void engine_run(const Box<T, NST> &bx, const P &pol, long long max_sweeps, char *smem, long long &sweeps,
-                           bool &converged, int *err) {
-    const int nw = bx.nb;
+                           bool &converged, int *err, T *ghands = nullptr, int *gctl = nullptr) {
+    const int nwc = GLOBAL ? (int)(blockDim.x >> 5) : bx.nb;   // warps (blocks) of this CTA
+    const int b0 = GLOBAL ? (int)blockIdx.x * nwc : 0;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const size_t ring_e = (size_t)RROWS * 32, sring_e = (size_t)NST * SRCH * CH * 32;
-    const size_t halo_e = RROWS, hand_e = (size_t)((bx.ny + 3) & ~3);
+    const size_t halo_e = RROWS, hand_e = GLOBAL ? (size_t)bx.ny : (size_t)((bx.ny + 3) & ~3);
     const size_t sb_b = HASB ? (size_t)SRCH * CH * 32 : 0;
     T *base = reinterpret_cast<T *>(smem);
     T *ring = base + (size_t)warp * ring_e;
-    T *sring = base + (size_t)nw * ring_e + (size_t)warp * sring_e;
-    T *halo = base + (size_t)nw * (ring_e + sring_e) + (size_t)warp * halo_e;
-    T *hands = base + (size_t)nw * (ring_e + sring_e + halo_e);
-    uint8_t *bytes = reinterpret_cast<uint8_t *>(hands + (size_t)nw * hand_e);
+    T *sring = base + (size_t)nwc * ring_e + (size_t)warp * sring_e;
+    T *halo = base + (size_t)nwc * (ring_e + sring_e) + (size_t)warp * halo_e;
+    T *hands;
+    uint8_t *bytes;
+    if (GLOBAL) {
+        hands = ghands;
+        bytes = reinterpret_cast<uint8_t *>(base + (size_t)nwc * (ring_e + sring_e + halo_e));
+    } else {
+        hands = base + (size_t)nwc * (ring_e + sring_e + halo_e);
+        bytes = reinterpret_cast<uint8_t *>(hands + (size_t)nwc * hand_e);
+    }
     uint8_t *sbring = bytes + (size_t)warp * sb_b;
-    int *ints = reinterpret_cast<int *>(bytes + (size_t)nw * sb_b);
+    int *ints = GLOBAL ? gctl : reinterpret_cast<int *>(bytes + (size_t)nwc * sb_b);
     EngineCtl C;
     C.abort_flag = ints;
     C.stop_at = ints + 1;
     C.fin = ints + 8;
     C.chg = ints + 16;
     C.prog = ints + 32;
-    C.done = ints + 32 + nw;
+    C.done = ints + 32 + bx.nb;
 
-    if (threadIdx.x == 0) {
-        C.abort_flag[0] = 0;
-        C.stop_at[0] = 0x7fffffff;
-    }
-    if (threadIdx.x < 8) {
-        C.fin[threadIdx.x] = 0;
-        C.chg[threadIdx.x] = 0;
-    }
-    if ((int)threadIdx.x < nw) {
-        C.prog[threadIdx.x] = -1;
-        C.done[threadIdx.x] = 0;
+    if (!GLOBAL) {
+        if (threadIdx.x == 0) {
+            C.abort_flag[0] = 0;
+            C.stop_at[0] = 0x7fffffff;
+        }
+        if (threadIdx.x < 8) {
+            C.fin[threadIdx.x] = 0;
+            C.chg[threadIdx.x] = 0;
+        }
+        if ((int)threadIdx.x < bx.nb) {
+            C.prog[threadIdx.x] = -1;
+            C.done[threadIdx.x] = 0;
+        }
     }
     __syncthreads();
 
-    if (warp < nw) {
-        const int b = warp;
+    const int b = b0 + warp;
+    if (warp < nwc && b < bx.nb) {
         T *hand = hands + (size_t)b * hand_e;
         for (long long kk = 0; kk < max_sweeps; ++kk) {
             const int k = (int)kk;
             if (vload(C.abort_flag) || vload(C.stop_at) < k) break;
             int ch;
             switch (k & 3) {
-                case 0: ch = run_block<-1, -1, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
-                case 1: ch = run_block<-1, +1, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
-                case 2: ch = run_block<+1, -1, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
-                default: ch = run_block<+1, +1, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                case 0: ch = run_block<-1, -1, GLOBAL, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                case 1: ch = run_block<-1, +1, GLOBAL, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                case 2: ch = run_block<+1, -1, GLOBAL, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                default: ch = run_block<+1, +1, GLOBAL, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
             }
             if (ch < 0) break;
             // sweep k of this block is complete: publish it, then the sweep status
             if (lane == 0) {
-                __threadfence_block();
+                fence<GLOBAL>();
                 vstore(C.done + b, k + 1);
                 if (ch) atomicOr(C.chg + (k & 7), 1);
-                __threadfence_block();
+                fence<GLOBAL>();
                 const int f = atomicAdd(C.fin + (k & 7), 1);
-                if (f == nw - 1) {
+                if (f == bx.nb - 1) {
                     if (vload(C.chg + (k & 7)) == 0) {
                         atomicMin(C.stop_at, k);
                     } else {
@@ -397,6 +444,16 @@ __device__ void engine_run(const Box<T, NST> &bx, const P &pol, long long max_sw
     converged = st != 0x7fffffff && !vload(C.abort_flag);
     sweeps = st != 0x7fffffff ? (long long)st + 1 : max_sweeps;
     __syncthreads();
+}
+
+// Zeroes the control words of a multi-CTA engine run (one thread block).
+__device__ inline void engine_global_init(int *gctl, int nb) {
+    for (int i = threadIdx.x; i < (int)engine_global_ints(nb); i += blockDim.x) {
+        int v = 0;
+        if (i == 1) v = 0x7fffffff;
+        if (i >= 32 && i < 32 + nb) v = -1;
+        gctl[i] = v;
+    }
 }
 
 }  // namespace eik

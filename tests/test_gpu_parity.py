@@ -150,3 +150,26 @@ def test_dd_fp32_converged_against_oracle(gpu):
                          **args)
     assert s_ref["converged"] == 1
     assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
+
+
+@pytest.mark.parametrize("shape", [(300, 1100), (40, 2049)])
+def test_fsm_multi_cta_fp64_bitwise(gpu, shape):
+    """Grids wider than one CTA's 32 blocks run on many co-resident CTAs with
+    global hand-offs: still the same sweeps, bitwise."""
+    r, gamma, g = _random_problem(shape, shape[1])
+    u_ref, s_ref, c_ref = O.fsm(r, gamma, g, 1.0 / 1024)
+    u, st = gpu.fsm(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), 1.0 / 1024)
+    assert st["converged"] == 1 and st["sweeps"] <= s_ref
+    np.testing.assert_array_equal(u.cpu().numpy(), u_ref)
+
+
+def test_fsm_full_size_fp32_against_oracle(gpu):
+    """The full 4097^2 workload of the benchmark (Fourier-mode slowness, left
+    edge source) through the plain FSM in FP32, against the FP64 oracle on the
+    same rounded slowness, element by element."""
+    w = I.workload_c1()
+    r32 = w["r"].astype(np.float32)
+    u_ref, s_ref, c_ref = O.fsm(r32.astype(np.float64), w["gamma"], w["g"], w["h"])
+    u, st = gpu.fsm(_t(r32, torch.float32), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float32), w["h"])
+    assert c_ref and st["converged"] == 1
+    assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
