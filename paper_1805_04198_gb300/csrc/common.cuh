@@ -93,11 +93,95 @@ __device__ __forceinline__ T local_solve2_value(T vmx, T vpx, T vmy, T vpy, T rh
     return fabs(d) < rh ? u2 : u1;
 }
 
+// 3-D Godunov local solve: axis minima sorted a_p0 <= a_p1 <= a_p2 (ties keep
+// axis order); one term, else the paper's two-term formula on the two
+// smallest, else the three-term quadratic written in t = u - a_p0:
+//   t^2 + (t - d1)^2 + (t - d2)^2 = (r h)^2.
+// The wind has the per-axis sign of Alg. 3 on the axes used.  With a_p2 = inf
+// it reduces exactly to local_solve2.
+template <class T>
+__device__ __forceinline__ T local_solve3(const T *vm, const T *vp, T rh, uint8_t &wind) {
+    using N = Num<T>;
+    T a[3];
+    int s[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool lm = vm[k] < vp[k];
+        a[k] = lm ? vm[k] : vp[k];
+        s[k] = lm ? 1 : -1;
+    }
+    int p0 = 0, p1 = 1, p2 = 2, t;
+    if (a[p1] < a[p0]) { t = p0; p0 = p1; p1 = t; }
+    if (a[p2] < a[p1]) {
+        t = p1; p1 = p2; p2 = t;
+        if (a[p1] < a[p0]) { t = p0; p0 = p1; p1 = t; }
+    }
+    int w[3] = {0, 0, 0};
+    T u;
+    const T d01 = N::sub(a[p0], a[p1]);
+    if (fabs(d01) < rh) {
+        const T disc = N::sub(N::mul(N::mul(T(2), rh), rh), N::mul(d01, d01));
+        u = N::mul(N::add(N::add(a[p0], a[p1]), N::sqrt_solve(fmax(disc, T(0)))), T(0.5));
+        if (u > a[p2]) {
+            const T d1 = N::sub(a[p1], a[p0]);
+            const T d2 = N::sub(a[p2], a[p0]);
+            const T sd = N::add(d1, d2);
+            T disc3 = N::sub(N::mul(sd, sd),
+                             N::mul(T(3), N::sub(N::add(N::mul(d1, d1), N::mul(d2, d2)), N::mul(rh, rh))));
+            if (disc3 < T(0)) disc3 = T(0);
+            u = N::add(a[p0], N::div(N::add(sd, N::sqrt_solve(disc3)), T(3)));
+            w[0] = s[0];
+            w[1] = s[1];
+            w[2] = s[2];
+        } else {
+            w[p0] = s[p0];
+            w[p1] = s[p1];
+        }
+    } else {
+        u = N::add(a[p0], rh);
+        if (u < N::inf()) w[p0] = s[p0];
+    }
+    wind = wind_pack(w[0], w[1], w[2]);
+    return u;
+}
+
 // Status codes mirrored from eik.h for device code.
 constexpr int DEV_OK = 0;
 constexpr int DEV_TIMEOUT = -4;
 
 // Bounded spin limit for every device-side wait (iterations of ~64 ns sleep).
 constexpr long long SPIN_LIMIT = 1ll << 22;
+
+// Grid-wide barrier for cooperative launches (all CTAs co-resident).  bar[0]
+// counts arrivals, bar[1] is the generation.  The wait is bounded: on timeout
+// the error word is set and false is returned (the caller then returns).
+__device__ inline bool grid_barrier(unsigned *bar, int *err) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == gen) {
+                if (++it > SPIN_LIMIT) {
+                    atomicExch(err, DEV_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok;
+}
 
 }  // namespace eik

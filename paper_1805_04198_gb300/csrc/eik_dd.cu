@@ -273,35 +273,6 @@ __device__ __forceinline__ void k_step4_body(DDArgs<T> &A, char *smem) {
 // --------------------------------------------------------------------------
 // Causal sweep (Alg. 2): least fixed point along every coarse line.
 // --------------------------------------------------------------------------
-__device__ inline bool grid_barrier(unsigned *bar, int *err) {
-    __syncthreads();
-    bool ok = true;
-    if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long it = 0;
-            while (*vgen == gen) {
-                if (++it > SPIN_LIMIT) {
-                    atomicExch(err, DEV_TIMEOUT);
-                    ok = false;
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok;
-}
-
 // One direction of one line: values v (current) with "connected to the
 // predecessor in scan order" flags; inclusive segmented max-scan per 32-node
 // chunk with a carry across chunks.
@@ -355,7 +326,7 @@ __device__ bool causal_line(const DDArgs<T> &A, bool horizontal, int line, int r
         carry = __shfl_sync(FULL, v, 31);
         carry_orig = __shfl_sync(FULL, u, 31);
     }
-    return changed;
+    return __any_sync(FULL, changed);  // warp-uniform: any lane raised a node
 }
 
 template <class T>
@@ -680,12 +651,27 @@ struct DDPlan {
     int grid_threads;
 };
 
+// 3-D implementation (eik_dd3.cu)
+size_t dd3_workspace_size(const eik_grid *grid, const eik_dd_params *p);
+bool dd3_validate(const eik_grid *grid, const eik_dd_params *p);
+int dd3_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, const eik_dd_params *p,
+            void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s);
+
 static bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
-    if (!valid_grid_common(grid, 2)) return false;
     if (!p) {
         set_error("params is NULL");
         return false;
     }
+    if (grid && grid->ndim == 3) {
+        if (!valid_grid_common(grid, 3)) return false;
+        if (p->max_iter < 0 || p->max_iter > 100000 || p->max_fsm_sweeps < 1 || p->max_coarse_sweeps < 1 ||
+            p->max_fsm_sweeps > MAX_SWEEPS || p->max_coarse_sweeps > MAX_SWEEPS || !std::isfinite(p->theta)) {
+            set_error("max_iter must be in [0, 100000], sweep caps in [1, %lld], theta finite", MAX_SWEEPS);
+            return false;
+        }
+        return dd3_validate(grid, p);
+    }
+    if (!valid_grid_common(grid, 2)) return false;
     for (int a = 0; a < 2; ++a) {
         if (p->tiles[a] < 1 || (grid->n[a] - 1) % p->tiles[a] != 0) {
             set_error("tiles[%d] = %d does not divide n[%d]-1 = %lld", a, p->tiles[a], a, (long long)(grid->n[a] - 1));
@@ -886,6 +872,7 @@ using namespace eik;
 
 extern "C" size_t eik_dd_workspace_size(const eik_grid *grid, const eik_dd_params *params) {
     if (!dd_validate(grid, params)) return 0;
+    if (grid->ndim == 3) return dd3_workspace_size(grid, params);
     return dd_plan(grid, params).bytes;
 }
 
@@ -901,12 +888,13 @@ extern "C" int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *
         set_error("workspace must be 256-byte aligned");
         return EIK_EINVAL;
     }
-    DDPlan P = dd_plan(grid, params);
-    if (ws_bytes < P.bytes) {
-        set_error("workspace of %zu bytes is smaller than the %zu required", ws_bytes, P.bytes);
+    const size_t need = grid->ndim == 3 ? dd3_workspace_size(grid, params) : dd_plan(grid, params).bytes;
+    if (ws_bytes < need) {
+        set_error("workspace of %zu bytes is smaller than the %zu required", ws_bytes, need);
         return EIK_ENOMEM;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grid->ndim == 3) return dd3_run(grid, r, gamma, g, params, u_out, ws, stats, s);
     if (grid->dtype == EIK_F64) return dd_run<double>(grid, r, gamma, g, params, u_out, ws, stats, s);
     return dd_run<float>(grid, r, gamma, g, params, u_out, ws, stats, s);
 }

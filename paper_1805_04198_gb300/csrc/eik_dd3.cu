@@ -1,0 +1,815 @@
+// eik_dd3.cu -- the two-scale DD iteration (Sec. 3.2, Steps 1-4, Alg. 1-5)
+// in three dimensions.  The paper states the method in 2-D and says it
+// "can be generalized"; the generalisation used here:
+//   * coarse set: every node with some index = 0 mod c, the union of the
+//     c^3 - (c-1)^3 shifted coarse grids (offsets with at least one zero);
+//   * Alg. 4 / Alg. 5 agreement tests on every interface / coarse-line axis
+//     of a node; the causal sweep (Alg. 2) along every axis e whose fine
+//     neighbours stay on the coarse set (the node lies on a coarse plane of
+//     another axis);
+//   * the 3-D Godunov local solve (sorted-minima cascade).
+// Subdomains and shifted coarse grids are small boxes that fit in shared
+// memory, so each is swept by one CTA along hyperplanes i + j + k = const
+// (nodes of a hyperplane are independent; a barrier separates hyperplanes),
+// which is the serial Gauss-Seidel order of the paper's loop nest.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "host_util.h"
+#include "prof.h"
+
+namespace eik {
+
+struct Grid3 {
+    int ox, oy, oz, mx, my, mz;
+    long long off;  // element offset in the coarse arrays ([z][y][x] box)
+};
+
+struct DD3Geom {
+    int n[3], T[3], S[3], c, ng;
+    long long nc;           // coarse elements
+    double h, H;
+};
+
+struct DevStats3 {
+    unsigned long long fsm_sweeps_max, coarse_sweeps_max, fsm_caps, coarse_caps, fine_updates, coarse_updates;
+    int causal_rounds_max, err, iters, converged;
+};
+
+template <class T>
+struct DD3Args {
+    DD3Geom G;
+    const T *r;
+    const uint8_t *gamma;
+    const T *g;
+    T *u_out;
+    long long sy, sz;
+    Grid3 *grids;
+    int *offmap;  // [c^3] offset -> grid index (-1 if not a shifted grid)
+    T *U, *Uprev, *U0, *rc, *uk, *cold;
+    uint8_t *W, *wk, *mask;
+    T *cu;
+    uint8_t *cw;
+    int *done;
+    double *deltas;
+    int *chg;
+    unsigned *bar;
+    DevStats3 *st;
+    T theta, tol;
+    int max_iter;
+    long long max_fsm, max_coarse;
+};
+
+template <class T>
+__device__ __forceinline__ size_t fidx(const DD3Args<T> &A, int X, int Y, int Z) {
+    return (size_t)Z * A.sz + (size_t)Y * A.sy + X;
+}
+
+template <class T>
+__device__ __forceinline__ long long coarse_addr3(const DD3Args<T> &A, int X, int Y, int Z) {
+    const int c = A.G.c;
+    const int g = A.offmap[((Z % c) * c + (Y % c)) * c + (X % c)];
+    const Grid3 d = A.grids[g];
+    return d.off + ((long long)(Z / c) * d.my + (Y / c)) * d.mx + (X / c);
+}
+
+__device__ __forceinline__ int coarse_axes3(int X, int Y, int Z, int c) {
+    return (X % c == 0 ? 1 : 0) | (Y % c == 0 ? 2 : 0) | (Z % c == 0 ? 4 : 0);
+}
+
+// --------------------------------------------------------------------------
+// Box sweeps in shared memory along hyperplanes.  Sweep k uses ordering
+// k mod 8 of the paper's loop nest: sign of x = bit 2, y = bit 1, z = bit 0.
+// The update functor returns the new value of a node from its neighbours.
+// --------------------------------------------------------------------------
+template <class T, class P>
+__device__ void box3_sweeps(T *su, int mx, int my, int mz, const P &pol, long long max_sweeps, long long &sweeps,
+                            bool &conv) {
+    const T INF = Num<T>::inf();
+    const int ndiag = mx + my + mz - 2;
+    sweeps = 0;
+    conv = false;
+    for (long long k = 0; k < max_sweeps; ++k) {
+        const int q = (int)(k & 7);
+        const int sx = (q & 4) ? 1 : -1, sy = (q & 2) ? 1 : -1, sz = (q & 1) ? 1 : -1;
+        bool ch = false;
+        for (int dg = 0; dg < ndiag; ++dg) {
+            const int ilo = max(0, dg - (my - 1) - (mz - 1));
+            const int ihi = min(mx - 1, dg);
+            const int ncand = (ihi - ilo + 1) * my;
+            for (int cnd = threadIdx.x; cnd < ncand; cnd += blockDim.x) {
+                const int ip = ilo + cnd / my, jp = cnd % my, kp = dg - ip - jp;
+                if (kp < 0 || kp >= mz) continue;
+                const int x = sx > 0 ? ip : mx - 1 - ip;
+                const int y = sy > 0 ? jp : my - 1 - jp;
+                const int z = sz > 0 ? kp : mz - 1 - kp;
+                const int idx = (z * my + y) * mx + x;
+                T vm[3], vp[3];
+                vm[0] = x > 0 ? su[idx - 1] : INF;
+                vp[0] = x + 1 < mx ? su[idx + 1] : INF;
+                vm[1] = y > 0 ? su[idx - mx] : INF;
+                vp[1] = y + 1 < my ? su[idx + mx] : INF;
+                vm[2] = z > 0 ? su[idx - mx * my] : INF;
+                vp[2] = z + 1 < mz ? su[idx + mx * my] : INF;
+                const T self = su[idx];
+                bool c1 = false;
+                const T nw = pol.update(self, vm, vp, x, y, z, idx, c1);
+                if (c1) {
+                    su[idx] = nw;
+                    ch = true;
+                }
+            }
+            __syncthreads();
+        }
+        ++sweeps;
+        if (!__syncthreads_or(ch ? 1 : 0)) {
+            conv = true;
+            break;
+        }
+    }
+}
+
+// FSM update (Sec. 1.1): u = min(u, u~) at free nodes.
+template <class T>
+struct Fsm3 {
+    const uint8_t *fixed;  // shared, per box node
+    const T *r;            // per box node, via rix
+    long long r0, rsx, rsy, rsz;  // global index of box node (x,y,z) = r0 + x*rsx + y*rsy + z*rsz
+    T hs;
+    __device__ __forceinline__ T update(T self, const T *vm, const T *vp, int x, int y, int z, int idx,
+                                        bool &changed) const {
+        if (fixed[idx]) return self;
+        const T rv = r[r0 + x * rsx + y * rsy + z * rsz];
+        uint8_t w;
+        const T ut = local_solve3(vm, vp, Num<T>::mul(rv, hs), w);
+        changed = ut < self;
+        return changed ? ut : self;
+    }
+};
+
+// Alg. 5 update on a shifted grid box (box layout arrays from `off`).
+template <class T>
+struct Alg5_3 {
+    const T *rc, *uk, *cold;
+    const uint8_t *mask;
+    long long off;
+    T Hs, theta;
+    __device__ __forceinline__ T update(T self, const T *vm, const T *vp, int, int, int, int idx,
+                                        bool &changed) const {
+        using N = Num<T>;
+        const long long a = off + idx;
+        const uint8_t m = mask[a];
+        if (m & 1) return self;
+        uint8_t w;
+        const T Ut = local_solve3(vm, vp, N::mul(rc[a], Hs), w);
+        const T ukv = uk[a], cv = cold[a];
+        bool pass = (Ut < N::inf()) && (cv < N::inf());
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const int wc = wind_comp(w, ax);
+            pass = pass && ((wc <= 0 && (m & (2 << (2 * ax)))) || (wc >= 0 && (m & (4 << (2 * ax)))));
+        }
+        const T nu = pass ? N::add(ukv, N::mul(theta, N::sub(Ut, cv))) : ukv;
+        changed = !(nu == self);
+        return nu;
+    }
+};
+
+// --------------------------------------------------------------------------
+// Set-up
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void k3_init(DD3Args<T> A) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        memset(A.st, 0, sizeof(DevStats3));
+        *A.done = 0;
+        A.bar[0] = A.bar[1] = 0;
+    }
+    for (int k = threadIdx.x; k < A.max_iter + 2; k += blockDim.x) A.deltas[k] = k == 0 ? INFINITY : 0.0;
+}
+
+// one CTA row per shifted grid (blockIdx.y), threads over its nodes
+template <class T>
+__global__ void k3_pack_coarse(DD3Args<T> A) {
+    const Grid3 d = A.grids[blockIdx.y];
+    const long long n = (long long)d.mx * d.my * d.mz;
+    const int c = A.G.c;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % d.mx), j = (int)((e / d.mx) % d.my), k = (int)(e / ((long long)d.mx * d.my));
+        const int X = d.ox + c * i, Y = d.oy + c * j, Z = d.oz + c * k;
+        const size_t f = fidx(A, X, Y, Z);
+        const bool gam = A.gamma[f] != 0;
+        const long long a = d.off + e;
+        A.rc[a] = gam ? T(-1) : A.r[f];
+        A.U0[a] = gam ? A.g[f] : Num<T>::inf();
+        A.W[a] = WIND_ZERO;
+    }
+}
+
+template <class T>
+__device__ void grid3_winds(const DD3Args<T> &A, const Grid3 &d, const T *su, T Hs) {
+    const T INF = Num<T>::inf();
+    const int n = d.mx * d.my * d.mz;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int x = e % d.mx, y = (e / d.mx) % d.my, z = e / (d.mx * d.my);
+        const long long a = d.off + e;
+        uint8_t w = WIND_ZERO;
+        const T rv = A.rc[a];
+        if (rv > T(0) && su[e] < INF) {
+            T vm[3], vp[3];
+            vm[0] = x > 0 ? su[e - 1] : INF;
+            vp[0] = x + 1 < d.mx ? su[e + 1] : INF;
+            vm[1] = y > 0 ? su[e - d.mx] : INF;
+            vp[1] = y + 1 < d.my ? su[e + d.mx] : INF;
+            vm[2] = z > 0 ? su[e - d.mx * d.my] : INF;
+            vp[2] = z + 1 < d.mz ? su[e + d.mx * d.my] : INF;
+            (void)local_solve3(vm, vp, Num<T>::mul(rv, Hs), w);
+        }
+        A.W[a] = w;
+    }
+}
+
+// Step 1: FSM with Alg. 1 on every shifted grid (one CTA per grid).
+template <class T>
+__global__ void k3_step1(DD3Args<T> A) {
+    extern __shared__ __align__(16) char smem[];
+    const Grid3 d = A.grids[blockIdx.x];
+    const int n = d.mx * d.my * d.mz;
+    T *su = reinterpret_cast<T *>(smem);
+    uint8_t *fx = reinterpret_cast<uint8_t *>(su + n);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        su[e] = A.U0[d.off + e];
+        fx[e] = A.rc[d.off + e] > T(0) ? 0 : 1;
+    }
+    __syncthreads();
+    Fsm3<T> pol{fx, A.rc, d.off, 1, d.mx, (long long)d.mx * d.my, T(A.G.H)};
+    long long sweeps;
+    bool conv;
+    box3_sweeps(su, d.mx, d.my, d.mz, pol, A.max_coarse, sweeps, conv);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) A.U[d.off + e] = su[e];
+    grid3_winds(A, d, su, T(A.G.H));
+    if (threadIdx.x == 0) {
+        atomicMax(&A.st->coarse_sweeps_max, (unsigned long long)sweeps);
+        if (!conv) atomicAdd(&A.st->coarse_caps, 1ull);
+        atomicAdd(&A.st->coarse_updates, (unsigned long long)sweeps * n);
+    }
+}
+
+// Step 4: Alg. 5 on every shifted grid.
+template <class T>
+__global__ void k3_step4(DD3Args<T> A) {
+    if (*A.done) return;
+    extern __shared__ __align__(16) char smem[];
+    const Grid3 d = A.grids[blockIdx.x];
+    const int n = d.mx * d.my * d.mz;
+    const T INF = Num<T>::inf();
+    const T Hs = T(A.G.H);
+    T *su = reinterpret_cast<T *>(smem);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) su[e] = A.U[d.off + e];
+    __syncthreads();
+    // C_H(nbrs^H(U^k)) and U^k for the delta
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int x = e % d.mx, y = (e / d.mx) % d.my, z = e / (d.mx * d.my);
+        const long long a = d.off + e;
+        A.Uprev[a] = su[e];
+        T vm[3], vp[3];
+        vm[0] = x > 0 ? su[e - 1] : INF;
+        vp[0] = x + 1 < d.mx ? su[e + 1] : INF;
+        vm[1] = y > 0 ? su[e - d.mx] : INF;
+        vp[1] = y + 1 < d.my ? su[e + d.mx] : INF;
+        vm[2] = z > 0 ? su[e - d.mx * d.my] : INF;
+        vp[2] = z + 1 < d.mz ? su[e + d.mx * d.my] : INF;
+        const T rv = A.rc[a];
+        uint8_t w;
+        A.cold[a] = local_solve3(vm, vp, Num<T>::mul(rv > T(0) ? rv : T(0), Hs), w);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) su[e] = A.U0[d.off + e];  // Sec. 1.1 initialisation
+    __threadfence_block();
+    __syncthreads();
+    Alg5_3<T> pol{A.rc, A.uk, A.cold, A.mask, d.off, Hs, A.theta};
+    long long sweeps;
+    bool conv;
+    box3_sweeps(su, d.mx, d.my, d.mz, pol, A.max_coarse, sweeps, conv);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        A.U[d.off + e] = su[e];
+        A.W[d.off + e] = A.wk[d.off + e];  // W = w^k
+    }
+    if (threadIdx.x == 0) {
+        atomicMax(&A.st->coarse_sweeps_max, (unsigned long long)sweeps);
+        if (!conv) atomicAdd(&A.st->coarse_caps, 1ull);
+        atomicAdd(&A.st->coarse_updates, (unsigned long long)sweeps * n);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Steps 2 + 3: one CTA per subdomain, the subdomain box in shared memory.
+// --------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ bool tile3_inflow(const DD3Args<T> &A, const int *l, const int *Xg, long long &ca) {
+    bool face = false;
+    for (int a = 0; a < 3; ++a) face = face || l[a] == 0 || l[a] == A.G.S[a];
+    if (!face) return false;
+    ca = coarse_addr3(A, Xg[0], Xg[1], Xg[2]);
+    const uint8_t w = A.W[ca];
+    bool in = false;
+    for (int a = 0; a < 3; ++a) {
+        const int wc = wind_comp(w, a);
+        in = in || (l[a] == 0 && wc > 0) || (l[a] == A.G.S[a] && wc < 0);
+    }
+    return in;
+}
+
+template <class T>
+__global__ void k3_fine(DD3Args<T> A) {
+    if (*A.done) return;
+    extern __shared__ __align__(16) char smem[];
+    const DD3Geom &G = A.G;
+    const int tile = blockIdx.x;
+    const int t0 = tile % G.T[0], t1 = (tile / G.T[0]) % G.T[1], t2 = tile / (G.T[0] * G.T[1]);
+    const int mx = G.S[0] + 1, my = G.S[1] + 1, mz = G.S[2] + 1;
+    const int n = mx * my * mz;
+    const T INF = Num<T>::inf();
+    T *su = reinterpret_cast<T *>(smem);
+    uint8_t *fx = reinterpret_cast<uint8_t *>(su + n);
+    const int b0 = t0 * G.S[0], b1 = t1 * G.S[1], b2 = t2 * G.S[2];
+    // Step 2: boundary data; interior and outflow nodes start at +inf
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int l[3] = {e % mx, (e / mx) % my, e / (mx * my)};
+        const int Xg[3] = {b0 + l[0], b1 + l[1], b2 + l[2]};
+        const size_t f = fidx(A, Xg[0], Xg[1], Xg[2]);
+        long long ca;
+        T v = INF;
+        uint8_t fixed = 0;
+        if (A.gamma[f]) {
+            v = A.g[f];
+            fixed = 1;
+        } else if (tile3_inflow(A, l, Xg, ca)) {
+            v = A.U[ca];
+            fixed = 2;
+        }
+        su[e] = v;
+        fx[e] = fixed;
+    }
+    __syncthreads();
+    Fsm3<T> pol{fx, A.r, (long long)fidx(A, b0, b1, b2), 1, A.sy, A.sz, T(G.h)};
+    long long sweeps;
+    bool conv;
+    box3_sweeps(su, mx, my, mz, pol, A.max_fsm, sweeps, conv);
+    if (threadIdx.x == 0) {
+        atomicMax(&A.st->fsm_sweeps_max, (unsigned long long)sweeps);
+        if (!conv) atomicAdd(&A.st->fsm_caps, 1ull);
+        atomicAdd(&A.st->fine_updates, (unsigned long long)sweeps * n);
+    }
+    // outputs: copies (u, w) at coarse-set nodes, fine values elsewhere
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int l[3] = {e % mx, (e / mx) % my, e / (mx * my)};
+        const int Xg[3] = {b0 + l[0], b1 + l[1], b2 + l[2]};
+        const size_t f = fidx(A, Xg[0], Xg[1], Xg[2]);
+        const T uv = su[e];
+        if (!coarse_axes3(Xg[0], Xg[1], Xg[2], G.c)) {
+            A.u_out[f] = uv;
+            continue;
+        }
+        const long long ca = coarse_addr3(A, Xg[0], Xg[1], Xg[2]);
+        uint8_t w = WIND_ZERO;
+        if (fx[e] == 2) {
+            w = A.W[ca];
+        } else if (fx[e] == 0 && uv < INF) {
+            T vm[3], vp[3];
+            vm[0] = l[0] > 0 ? su[e - 1] : INF;
+            vp[0] = l[0] + 1 < mx ? su[e + 1] : INF;
+            vm[1] = l[1] > 0 ? su[e - mx] : INF;
+            vp[1] = l[1] + 1 < my ? su[e + mx] : INF;
+            vm[2] = l[2] > 0 ? su[e - mx * my] : INF;
+            vp[2] = l[2] + 1 < mz ? su[e + mx * my] : INF;
+            (void)local_solve3(vm, vp, Num<T>::mul(A.r[f], T(G.h)), w);
+        }
+        int slot = 0;
+        for (int a = 0; a < 3; ++a)
+            if (Xg[a] % G.S[a] == 0 && Xg[a] > 0 && Xg[a] < G.n[a] - 1 && l[a] == 0) slot |= 1 << a;
+        A.cu[(size_t)slot * G.nc + ca] = uv;
+        A.cw[(size_t)slot * G.nc + ca] = w;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Alg. 4 and the inputs of Alg. 5
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void k3_alg4(DD3Args<T> A) {
+    if (*A.done) return;
+    const DD3Geom &G = A.G;
+    const Grid3 d = A.grids[blockIdx.y];
+    const long long n = (long long)d.mx * d.my * d.mz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int Xg[3] = {d.ox + G.c * (int)(e % d.mx), d.oy + G.c * (int)((e / d.mx) % d.my),
+                           d.oz + G.c * (int)(e / ((long long)d.mx * d.my))};
+        const long long a = d.off + e;
+        int B = 0;
+        for (int ax = 0; ax < 3; ++ax)
+            if (Xg[ax] % G.S[ax] == 0 && Xg[ax] > 0 && Xg[ax] < G.n[ax] - 1) B |= 1 << ax;
+        const uint8_t Wk = A.W[a];
+        int best = 0;
+        if (B) {
+            int sel = 0;
+            bool ok = true;
+            for (int ax = 0; ax < 3 && ok; ++ax) {
+                if (!(B & (1 << ax))) continue;
+                bool allneg = wind_comp(Wk, ax) <= 0, allpos = wind_comp(Wk, ax) >= 0;
+                for (int s = 0; s < 8; ++s) {
+                    if (s & ~B) continue;
+                    const int wv = wind_comp(A.cw[(size_t)s * G.nc + a], ax);
+                    if (wv > 0) allneg = false;
+                    if (wv < 0) allpos = false;
+                }
+                // Alg. 4: wind toward -axis -> plus-side copy (first branch)
+                if (allneg) sel |= 1 << ax;
+                else if (!allpos) ok = false;
+            }
+            if (ok) {
+                best = sel;
+            } else {
+                // minimum; ties keep the lowest subdomain index (slot order)
+                T bv = A.cu[a];
+                for (int s = 1; s < 8; ++s) {
+                    if (s & ~B) continue;
+                    const T v = A.cu[(size_t)s * G.nc + a];
+                    if (v < bv) {
+                        bv = v;
+                        best = s;
+                    }
+                }
+            }
+        }
+        const T ukv = A.cu[(size_t)best * G.nc + a];
+        const uint8_t wkv = A.cw[(size_t)best * G.nc + a];
+        A.uk[a] = ukv;
+        A.wk[a] = wkv;
+        const size_t f = fidx(A, Xg[0], Xg[1], Xg[2]);
+        A.u_out[f] = ukv;
+        uint8_t m = A.gamma[f] ? 1 : 0;
+        for (int ax = 0; ax < 3; ++ax) {
+            const bool on = Xg[ax] % G.c == 0;
+            const int wf = wind_comp(wkv, ax), wc = wind_comp(Wk, ax);
+            if (!on || (wf <= 0 && wc <= 0)) m |= 2 << (2 * ax);
+            if (!on || (wf >= 0 && wc >= 0)) m |= 4 << (2 * ax);
+        }
+        A.mask[a] = m;
+    }
+}
+
+template <class T>
+__global__ void k3_check(DD3Args<T> A, int k) {
+    if (*A.done) return;
+    const double delta = A.deltas[k];
+    const bool conv = k >= 1 && delta < (double)A.tol;
+    if (k == A.max_iter || conv) {
+        *A.done = 1;
+        A.st->iters = k;
+        A.st->converged = conv ? 1 : 0;
+    }
+}
+
+template <class T>
+__global__ void k3_delta(DD3Args<T> A, int k) {
+    if (*A.done) return;
+    double m = 0.0;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < A.G.nc;
+         a += (long long)gridDim.x * blockDim.x) {
+        const T u1 = A.U[a], u0 = A.Uprev[a];
+        if (u1 == u0) continue;
+        const double dv = fabs((double)u1 - (double)u0);
+        if (dv > m) m = dv;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long *>(&A.deltas[k + 1]), (unsigned long long)__double_as_longlong(m));
+}
+
+// --------------------------------------------------------------------------
+// Causal sweep (Alg. 2): every line along axis e whose nodes lie on a coarse
+// plane of another axis; least fixed point by segmented max-scans, rounds
+// until nothing changes.
+// --------------------------------------------------------------------------
+template <class T>
+__device__ bool causal3_line(const DD3Args<T> &A, int e, int c1, int c2, int rev) {
+    const DD3Geom &G = A.G;
+    const T INF = Num<T>::inf();
+    const int lane = threadIdx.x & 31;
+    const int len = G.n[e];
+    const int a1 = (e + 1) % 3, a2 = (e + 2) % 3;
+    bool changed = false;
+    T carry = INF, carry_orig = INF;
+    for (int ch = 0; ch < (len + 31) / 32; ++ch) {
+        const int pos = ch * 32 + lane;
+        const bool valid = pos < len;
+        const int p = rev ? len - 1 - pos : pos;
+        int Xg[3];
+        Xg[e] = p;
+        Xg[a1] = c1;
+        Xg[a2] = c2;
+        long long a = 0;
+        T u = INF;
+        int wc = 0;
+        if (valid) {
+            a = coarse_addr3(A, Xg[0], Xg[1], Xg[2]);
+            u = __ldcg(A.U + a);
+            wc = wind_comp(__ldcg(A.W + a), e);
+        }
+        T pred_orig = __shfl_up_sync(FULL, u, 1);
+        if (lane == 0) pred_orig = carry_orig;
+        bool ff = valid && pos > 0 && (rev ? wc < 0 : wc > 0) && (pred_orig < INF);
+        T v = u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T vo = __shfl_up_sync(FULL, v, o);
+            const bool fo = __shfl_up_sync(FULL, ff ? 1 : 0, o) != 0;
+            if (lane >= o && ff) {
+                v = fmax(v, vo);
+                ff = fo;
+            }
+        }
+        if (ff) v = fmax(v, carry);
+        if (valid && v > u) {
+            A.U[a] = v;
+            changed = true;
+        }
+        carry = __shfl_sync(FULL, v, 31);
+        carry_orig = __shfl_sync(FULL, u, 31);
+    }
+    return __any_sync(FULL, changed);  // warp-uniform: any lane raised a node
+}
+
+template <class T>
+__global__ void k3_causal(DD3Args<T> A, int only_if_not_done) {
+    if (only_if_not_done && *A.done) return;
+    const DD3Geom &G = A.G;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    __shared__ int blk_changed;
+    if (blockIdx.x == 0 && threadIdx.x < 3) A.chg[threadIdx.x] = 0;
+    if (!grid_barrier(A.bar, &A.st->err)) return;
+    int rounds = 0;
+    for (;;) {
+        if (threadIdx.x == 0) blk_changed = 0;
+        __syncthreads();
+        bool ch = false;
+        for (int e = 0; e < 3; ++e) {
+            const int a1 = (e + 1) % 3, a2 = (e + 2) % 3;
+            const int n1 = G.n[a1], n2 = G.n[a2];
+            for (int L = gw; L < n1 * n2; L += warps_total) {
+                const int c1 = L % n1, c2 = L / n1;
+                if (c1 % G.c != 0 && c2 % G.c != 0) continue;  // not on the coarse set
+                ch |= causal3_line(A, e, c1, c2, 0);
+                ch |= causal3_line(A, e, c1, c2, 1);
+            }
+            if (!grid_barrier(A.bar, &A.st->err)) return;
+        }
+        if (lane == 0 && ch) atomicOr(&blk_changed, 1);
+        __syncthreads();
+        if (threadIdx.x == 0 && blk_changed) atomicOr(&A.chg[rounds % 3], 1);
+        ++rounds;
+        if (!grid_barrier(A.bar, &A.st->err)) return;
+        const int any = *(volatile int *)&A.chg[(rounds - 1) % 3];
+        if (blockIdx.x == 0 && threadIdx.x == 0) A.chg[(rounds + 1) % 3] = 0;
+        if (!any || rounds > 10000) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&A.st->causal_rounds_max, rounds);
+}
+
+template <class T>
+__global__ void k3_finalize(DD3Args<T> A, eik_dd_stats *out, long long launches) {
+    if (threadIdx.x != 0 || !out) return;
+    out->iters = A.st->iters;
+    out->converged = A.st->converged;
+    out->error = A.st->err;
+    out->causal_rounds_max = A.st->causal_rounds_max;
+    out->fsm_sweeps_max = (int64_t)A.st->fsm_sweeps_max;
+    out->coarse_sweeps_max = (int64_t)A.st->coarse_sweeps_max;
+    out->fsm_cap_hits = (int64_t)A.st->fsm_caps;
+    out->coarse_cap_hits = (int64_t)A.st->coarse_caps;
+    const int k = A.st->iters;
+    out->last_delta = k >= 1 ? A.deltas[k] : INFINITY;
+    out->fine_updates = (int64_t)A.st->fine_updates;
+    out->coarse_updates = (int64_t)A.st->coarse_updates;
+    out->launches = launches;
+}
+
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+struct DD3Plan {
+    DD3Geom G;
+    std::vector<Grid3> grids;
+    std::vector<int> offmap;
+    size_t fine_smem, grid_smem, bytes;
+    int fine_threads, grid_threads;
+};
+
+static bool dd3_plan(const eik_grid *grid, const eik_dd_params *p, DD3Plan &P) {
+    const int c = p->coarse_ratio;
+    DD3Geom &G = P.G;
+    for (int a = 0; a < 3; ++a) {
+        G.n[a] = (int)grid->n[a];
+        G.T[a] = p->tiles[a];
+        G.S[a] = (G.n[a] - 1) / G.T[a];
+    }
+    G.c = c;
+    G.h = grid->h;
+    G.H = (double)c * grid->h;
+    P.grids.clear();
+    P.offmap.assign((size_t)c * c * c, -1);
+    long long off = 0;
+    for (int oz = 0; oz < c; ++oz)
+        for (int oy = 0; oy < c; ++oy)
+            for (int ox = 0; ox < c; ++ox) {
+                if (ox && oy && oz) continue;
+                Grid3 d;
+                d.ox = ox;
+                d.oy = oy;
+                d.oz = oz;
+                d.mx = (G.n[0] - 1 - ox) / c + 1;
+                d.my = (G.n[1] - 1 - oy) / c + 1;
+                d.mz = (G.n[2] - 1 - oz) / c + 1;
+                d.off = off;
+                off += (long long)d.mx * d.my * d.mz;
+                P.offmap[((size_t)oz * c + oy) * c + ox] = (int)P.grids.size();
+                P.grids.push_back(d);
+            }
+    G.ng = (int)P.grids.size();
+    G.nc = off;
+    const size_t tsz = grid->dtype == EIK_F64 ? 8 : 4;
+    const size_t tile_n = (size_t)(G.S[0] + 1) * (G.S[1] + 1) * (G.S[2] + 1);
+    size_t gmax = 0;
+    for (auto &d : P.grids) gmax = std::max(gmax, (size_t)d.mx * d.my * d.mz);
+    P.fine_smem = tile_n * (tsz + 1) + 16;
+    P.grid_smem = gmax * (tsz + 1) + 16;
+    P.fine_threads = 512;
+    P.grid_threads = 512;
+    return true;
+}
+
+template <class T>
+static size_t dd3_layout(const DD3Plan &P, DD3Args<T> *A, void *ws, int max_iter) {
+    const DD3Geom &G = P.G;
+    Carver cv(ws);
+    T *U = cv.take<T>(G.nc), *Uprev = cv.take<T>(G.nc), *U0 = cv.take<T>(G.nc), *rc = cv.take<T>(G.nc);
+    T *uk = cv.take<T>(G.nc), *cold = cv.take<T>(G.nc);
+    uint8_t *W = cv.take<uint8_t>(G.nc), *wk = cv.take<uint8_t>(G.nc), *mask = cv.take<uint8_t>(G.nc);
+    T *cu = cv.take<T>(8 * (size_t)G.nc);
+    uint8_t *cw = cv.take<uint8_t>(8 * (size_t)G.nc);
+    Grid3 *grids = cv.take<Grid3>(P.grids.size());
+    int *offmap = cv.take<int>(P.offmap.size());
+    int *done = cv.take<int>(4);
+    double *deltas = cv.take<double>((size_t)max_iter + 2);
+    int *chg = cv.take<int>(4);
+    unsigned *bar = cv.take<unsigned>(4);
+    DevStats3 *st = cv.take<DevStats3>(1);
+    if (A) {
+        A->U = U; A->Uprev = Uprev; A->U0 = U0; A->rc = rc; A->uk = uk; A->cold = cold;
+        A->W = W; A->wk = wk; A->mask = mask; A->cu = cu; A->cw = cw;
+        A->grids = grids; A->offmap = offmap; A->done = done; A->deltas = deltas; A->chg = chg; A->bar = bar;
+        A->st = st;
+    }
+    return cv.used + 256;
+}
+
+// Shifted-grid tables, built on the device in the enumeration order of the
+// host plan (z offset outermost, x innermost; offsets with no zero skipped).
+__global__ void k3_tables(Grid3 *grids, int *offmap, int c, int n0, int n1, int n2) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long off = 0;
+    int gi = 0;
+    for (int oz = 0; oz < c; ++oz)
+        for (int oy = 0; oy < c; ++oy)
+            for (int ox = 0; ox < c; ++ox) {
+                const int m = (oz * c + oy) * c + ox;
+                if (ox && oy && oz) {
+                    offmap[m] = -1;
+                    continue;
+                }
+                Grid3 d;
+                d.ox = ox;
+                d.oy = oy;
+                d.oz = oz;
+                d.mx = (n0 - 1 - ox) / c + 1;
+                d.my = (n1 - 1 - oy) / c + 1;
+                d.mz = (n2 - 1 - oz) / c + 1;
+                d.off = off;
+                off += (long long)d.mx * d.my * d.mz;
+                offmap[m] = gi;
+                grids[gi++] = d;
+            }
+}
+
+size_t dd3_workspace_size(const eik_grid *grid, const eik_dd_params *p) {
+    DD3Plan P;
+    dd3_plan(grid, p, P);
+    return grid->dtype == EIK_F64 ? dd3_layout<double>(P, nullptr, nullptr, p->max_iter)
+                                  : dd3_layout<float>(P, nullptr, nullptr, p->max_iter);
+}
+
+bool dd3_validate(const eik_grid *grid, const eik_dd_params *p) {
+    for (int a = 0; a < 3; ++a) {
+        if (p->tiles[a] < 1 || (grid->n[a] - 1) % p->tiles[a] != 0) {
+            set_error("tiles[%d] = %d does not divide n[%d]-1", a, p->tiles[a], a);
+            return false;
+        }
+        if (((grid->n[a] - 1) / p->tiles[a]) % p->coarse_ratio != 0) {
+            set_error("coarse_ratio %d does not divide the subdomain width along axis %d", p->coarse_ratio, a);
+            return false;
+        }
+    }
+    if (p->coarse_ratio < 1 || p->coarse_ratio > 64) {
+        set_error("coarse_ratio must be in [1, 64] in 3-D");
+        return false;
+    }
+    return true;
+}
+
+template <class T>
+static int dd3_run_t(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                     const eik_dd_params *p, void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s) {
+    DD3Plan P;
+    dd3_plan(grid, p, P);
+    DD3Args<T> A;
+    memset(&A, 0, sizeof(A));
+    A.G = P.G;
+    A.r = static_cast<const T *>(r);
+    A.gamma = gamma;
+    A.g = static_cast<const T *>(g);
+    A.u_out = static_cast<T *>(u_out);
+    A.sy = grid->stride[1];
+    A.sz = grid->stride[2];
+    dd3_layout<T>(P, &A, ws, p->max_iter);
+    A.theta = (T)p->theta;
+    A.tol = (T)p->tol;
+    A.max_iter = p->max_iter;
+    A.max_fsm = p->max_fsm_sweeps;
+    A.max_coarse = p->max_coarse_sweeps;
+    const DD3Geom &G = P.G;
+    int rc, dev, nsm = 0, optin = 0;
+    if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((int)P.fine_smem > optin || (int)P.grid_smem > optin) {
+        set_error("3-D subdomain or coarse grid box needs %zu / %zu bytes of shared memory (limit %d)", P.fine_smem,
+                  P.grid_smem, optin);
+        return EIK_EUNSUPPORTED;
+    }
+    if ((rc = cuda_check(cudaFuncSetAttribute(k3_fine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.fine_smem), "attr")))
+        return rc;
+    if ((rc = cuda_check(cudaFuncSetAttribute(k3_step1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grid_smem), "attr")))
+        return rc;
+    if ((rc = cuda_check(cudaFuncSetAttribute(k3_step4<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grid_smem), "attr")))
+        return rc;
+    const int causal_threads = 256;
+    int per_sm = 0;
+    if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_causal<T>, causal_threads, 0), "occ")))
+        return rc;
+    const int causal_blocks = std::max(1, std::min(per_sm * nsm, 2 * nsm));
+    const int ntiles = G.T[0] * G.T[1] * G.T[2];
+    dim3 cgrid(8, G.ng);
+    const int ew = 256;
+    const int eb = (int)std::min<long long>((G.nc + ew - 1) / ew, (long long)nsm * 8);
+    long long nl = 0;
+    EIK_LAUNCH("dd3_init", s, k3_init<T><<<1, 256, 0, s>>>(A)); ++nl;
+    EIK_LAUNCH("dd3_tables", s, k3_tables<<<1, 32, 0, s>>>(A.grids, A.offmap, G.c, G.n[0], G.n[1], G.n[2])); ++nl;
+    EIK_LAUNCH("dd3_pack_coarse", s, k3_pack_coarse<T><<<cgrid, ew, 0, s>>>(A)); ++nl;
+    EIK_LAUNCH("dd3_step1_coarse_fsm", s, k3_step1<T><<<G.ng, P.grid_threads, P.grid_smem, s>>>(A)); ++nl;
+    auto launch_causal = [&](int only) -> int {
+        void *args[] = {&A, &only};
+        int tok = prof_begin("dd3_causal_sweep", s);
+        int r2 = cuda_check(cudaLaunchCooperativeKernel((void *)k3_causal<T>, causal_blocks, causal_threads, args, 0, s),
+                            "causal launch");
+        prof_end(tok, s);
+        ++nl;
+        return r2;
+    };
+    if ((rc = launch_causal(0))) return rc;
+    for (int k = 0; k <= p->max_iter; ++k) {
+        EIK_LAUNCH("dd3_fine_subdomains", s, k3_fine<T><<<ntiles, P.fine_threads, P.fine_smem, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd3_alg4_restrict", s, k3_alg4<T><<<cgrid, ew, 0, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd3_check", s, k3_check<T><<<1, 1, 0, s>>>(A, k)); ++nl;
+        if (k == p->max_iter) break;
+        EIK_LAUNCH("dd3_step4_weighted", s, k3_step4<T><<<G.ng, P.grid_threads, P.grid_smem, s>>>(A)); ++nl;
+        if ((rc = launch_causal(1))) return rc;
+        EIK_LAUNCH("dd3_delta", s, k3_delta<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
+    }
+    ++nl;
+    EIK_LAUNCH("dd3_finalize", s, k3_finalize<T><<<1, 32, 0, s>>>(A, stats, nl));
+    return cuda_check(cudaGetLastError(), "dd3 launch");
+}
+
+int dd3_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, const eik_dd_params *p,
+            void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s) {
+    if (grid->dtype == EIK_F64) return dd3_run_t<double>(grid, r, gamma, g, p, u_out, ws, stats, s);
+    return dd3_run_t<float>(grid, r, gamma, g, p, u_out, ws, stats, s);
+}
+
+}  // namespace eik

@@ -173,3 +173,39 @@ def test_fsm_full_size_fp32_against_oracle(gpu):
     u, st = gpu.fsm(_t(r32, torch.float32), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float32), w["h"])
     assert c_ref and st["converged"] == 1
     assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
+
+
+def _dd3_case(n, amp=0.4, eps=0.25, src=None):
+    h = 1.0 / (n - 1)
+    r = I.sin_product((n, n, n), h, amp, eps)
+    gamma, g = I.point_source((n, n, n), src if src is not None else (n // 2, n // 2, n // 2))
+    return r, gamma, g, h
+
+
+@pytest.mark.parametrize("n,tiles,c,theta,kmax", [
+    (17, (2, 2, 2), 4, 0.5, 4),
+    (17, (2, 2, 2), 8, 0.2, 3),    # c equal to the subdomain width
+    (25, (3, 3, 3), 4, 0.5, 3),
+    (17, (1, 2, 4), 2, 1.0, 2),    # anisotropic tiling, theta = 1
+])
+def test_dd3_fp64_bitwise(gpu, n, tiles, c, theta, kmax):
+    r, gamma, g, h = _dd3_case(n, src=(n // 2, n // 3, n // 2))
+    for k in range(kmax + 1):
+        u_ref, s_ref, _ = O.dd(r, gamma, g, h, tiles, c, theta=theta, max_iter=k, tol=0.0, max_coarse_sweeps=16)
+        u, st = gpu.dd_solve(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h, tiles, c,
+                             theta=theta, max_iter=k, tol=0.0, max_coarse_sweeps=16)
+        assert st["iters"] == s_ref["iters"] == k
+        assert st["fsm_sweeps_max"] == s_ref["fsm_sweeps_max"]
+        np.testing.assert_array_equal(u.cpu().numpy(), u_ref, err_msg="k=%d" % k)
+
+
+def test_dd3_fp32_converged_against_oracle(gpu):
+    r, gamma, g, h = _dd3_case(33)
+    r32 = r.astype(np.float32)
+    # tol above the FP32 spacing of u ~ 1 so the FP32 run can meet it
+    args = dict(theta=0.3, max_iter=30, tol=2e-6, max_coarse_sweeps=32)
+    u_ref, s_ref, _ = O.dd(r32.astype(np.float64), gamma, g, h, (4, 4, 4), 8, **args)
+    u, st = gpu.dd_solve(_t(r32, torch.float32), _t(gamma, torch.uint8), _t(g, torch.float32), h, (4, 4, 4), 8,
+                         **args)
+    assert s_ref["converged"] == 1 and st["converged"] == 1
+    assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
