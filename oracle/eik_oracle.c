@@ -916,15 +916,17 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
 
 /* ------------------------------------------------------------------------- */
 /* Adjoint of the converged discrete system (a project addition; the paper has */
-/* no gradient).  At a converged u every reached non-Gamma node satisfies       */
-/* u_i = F(a_i, r_i) with a_i the per-axis neighbour minima of the branch the   */
-/* local solve takes.  Linearising: du_i = sum_j dF/da_j du_j + dF/dr_i dr_i,   */
-/* where j runs over the neighbours used, all with smaller u (causality).  For  */
-/* a scalar J(u), lambda = dJ/du + sum over downwind k of lambda_k dF_k/du_i,   */
-/* solved by visiting nodes in decreasing u; dJ/dr_i = lambda_i dF_i/dr_i.      */
+/* no gradient).  At a converged u every reached non-Gamma node j satisfies     */
+/* u_j = F(a_j, r_j), a_j the per-axis neighbour minima of the branch the local */
+/* solve takes (Alg. 3 choice, ties to the plus side).  Linearising:            */
+/*   du_j = sum_{i used by j} dF_j/du_i du_i + dF_j/dr_j dr_j,                  */
+/* with the used neighbours i all smaller than u_j (causality).  For a scalar J */
+/* with dJ/du given, lambda = dJ/du + (dF/du)^T lambda; each lambda_i pulls     */
+/* from the downwind neighbours j that use i, so visiting nodes in decreasing u */
+/* gives lambda exactly.  dJ/dr_j = lambda_j dF_j/dr_j.                         */
 /* Branch derivatives: one term dF/da = 1, dF/dr = h; several terms with        */
-/* sum_j (u - a_j)^2 = (r h)^2: dF/da_j = (u-a_j)/D, dF/dr = r h^2 / D,         */
-/* D = sum_j (u - a_j).                                                         */
+/* sum_k (u - a_k)^2 = (r h)^2: dF/da_k = (u - a_k)/D, dF/dr = r h h / D,       */
+/* D = sum_k (u - a_k) over the used axes in axis order.                        */
 /* ------------------------------------------------------------------------- */
 static int cmp_desc(const void *A, const void *B)
 {
@@ -932,6 +934,45 @@ static int cmp_desc(const void *A, const void *B)
     if (a->v > b->v) return -1;
     if (a->v < b->v) return 1;
     return (a->i < b->i) ? -1 : (a->i > b->i);
+}
+
+/* Weight dF_j/du_{j+off} with which node j depends on its neighbour j+off (0
+ * if j does not use that neighbour), and dF_j/dr_j. */
+static void adj_node(int d, const long *m, double h, const double *r, const unsigned char *gamma, const double *u,
+                     long j, double wm[3], double wp[3], double *dudr)
+{
+    long c[3];
+    double vm[3], vp[3], D = 0.0;
+    signed char w[3];
+    int k, used = 0;
+    for (k = 0; k < 3; ++k) wm[k] = wp[k] = 0.0;
+    *dudr = 0.0;
+    if (gamma[j] || !(u[j] < INF)) return;
+    c[0] = j % m[0];
+    c[1] = (j / m[0]) % m[1];
+    c[2] = j / (m[0] * m[1]);
+    nbrs(d, m, u, c[0], c[1], c[2], vm, vp);
+    (void)orc_local_solve(d, vm, vp, r[j] * h, w);
+    for (k = 0; k < d; ++k)
+        if (w[k] != 0) {
+            D = D + (u[j] - (w[k] > 0 ? vm[k] : vp[k]));
+            ++used;
+        }
+    if (used == 0) return;
+    if (used == 1) {
+        for (k = 0; k < d; ++k) {
+            if (w[k] > 0) wm[k] = 1.0;
+            if (w[k] < 0) wp[k] = 1.0;
+        }
+        *dudr = h;
+        return;
+    }
+    if (!(D > 0.0)) return;
+    for (k = 0; k < d; ++k) {
+        if (w[k] > 0) wm[k] = (u[j] - vm[k]) / D;
+        if (w[k] < 0) wp[k] = (u[j] - vp[k]) / D;
+    }
+    *dudr = ((r[j] * h) * h) / D;
 }
 
 void orc_adjoint(int d, const long *n, double h, const double *r, const unsigned char *gamma,
@@ -943,47 +984,40 @@ void orc_adjoint(int d, const long *n, double h, const double *r, const unsigned
     hent *ord = malloc(sizeof(hent) * (size_t)N);
     double *lam = malloc(sizeof(double) * (size_t)N);
     for (i = 0; i < N; ++i) {
-        lam[i] = dJdu[i];
+        lam[i] = 0.0;
         dJdr[i] = 0.0;
-        if (!gamma[i] && u[i] < INF) {
-            ord[cnt].v = u[i];
-            ord[cnt].i = i;
-            ++cnt;
-        }
+        ord[cnt].v = u[i] < INF ? u[i] : HUGE_VAL;
+        ord[cnt].i = i;
+        ++cnt;
     }
     qsort(ord, (size_t)cnt, sizeof(hent), cmp_desc);
     for (i = 0; i < cnt; ++i) {
         long j = ord[i].i, c[3];
-        double vm[3], vp[3], ut, D = 0.0;
-        signed char w[3];
-        long nb[3];
-        int k, used = 0;
+        int k;
+        double acc = dJdu[j];
         c[0] = j % m[0];
         c[1] = (j / m[0]) % m[1];
         c[2] = j / (m[0] * m[1]);
-        nbrs(d, m, u, c[0], c[1], c[2], vm, vp);
-        ut = orc_local_solve(d, vm, vp, r[j] * h, w);
-        (void)ut;
+        /* pull from the neighbours in the order -x, +x, -y, +y, -z, +z */
         for (k = 0; k < d; ++k) {
-            nb[k] = -1;
-            if (w[k] > 0) nb[k] = j - st[k]; /* upwind on the minus side */
-            if (w[k] < 0) nb[k] = j + st[k];
-            if (nb[k] >= 0) {
-                D += u[j] - u[nb[k]];
-                ++used;
+            int sd;
+            for (sd = -1; sd <= 1; sd += 2) {
+                double wm[3], wp[3], dr, wgt;
+                long nb;
+                if ((sd < 0 && c[k] == 0) || (sd > 0 && c[k] == m[k] - 1)) continue;
+                nb = j + sd * st[k];
+                adj_node(d, m, h, r, gamma, u, nb, wm, wp, &dr);
+                /* node nb depends on j through its minus side if j is below it */
+                wgt = sd > 0 ? wm[k] : wp[k];
+                if (wgt != 0.0) acc = acc + wgt * lam[nb];
             }
         }
-        if (used == 0) continue;
-        if (used == 1) {
-            for (k = 0; k < d; ++k)
-                if (nb[k] >= 0) lam[nb[k]] += lam[j];
-            dJdr[j] = lam[j] * h;
-        } else {
-            if (!(D > 0.0)) continue;
-            for (k = 0; k < d; ++k)
-                if (nb[k] >= 0) lam[nb[k]] += lam[j] * (u[j] - u[nb[k]]) / D;
-            dJdr[j] = lam[j] * r[j] * h * h / D;
-        }
+        lam[j] = acc;
+    }
+    for (i = 0; i < N; ++i) {
+        double wm[3], wp[3], dr;
+        adj_node(d, m, h, r, gamma, u, i, wm, wp, &dr);
+        dJdr[i] = lam[i] * dr;
     }
     free(ord);
     free(lam);

@@ -274,7 +274,7 @@ def test_adjoint_matches_finite_differences():
 
 def test_dd3_single_subdomain_is_fsm_and_converges():
     """3-D: one subdomain reproduces the plain FSM bitwise; with 4^3
-    subdomains and theta = 0.5 the iteration settles on the fine solution."""
+    subdomains and theta = 0.2 the iteration settles on the fine solution."""
     n = 17
     h = 1.0 / 16
     x = np.arange(n) * h
@@ -285,6 +285,6 @@ def test_dd3_single_subdomain_is_fsm_and_converges():
     uf, _, _ = O.fsm(r, gamma, 0.0, h)
     u1, _, _ = O.dd(r, gamma, 0.0, h, (1, 1, 1), 4, theta=0.5, max_iter=1, tol=-1)
     assert np.array_equal(u1, uf)
-    u, st, _ = O.dd(r, gamma, 0.0, h, (4, 4, 4), 4, theta=0.5, max_iter=30, tol=1e-13, max_coarse_sweeps=16)
+    u, st, _ = O.dd(r, gamma, 0.0, h, (4, 4, 4), 4, theta=0.2, max_iter=40, tol=1e-12, max_coarse_sweeps=16)
     assert st["converged"] == 1
-    assert np.max(np.abs(u - uf)) < 1e-6 * np.max(uf)
+    assert np.max(np.abs(u - uf)) < 1e-10 * np.max(uf)
