@@ -140,6 +140,41 @@ int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, cons
                  const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes,
                  eik_dd_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------------- */
+/* Gradient through the converged discrete system (a project addition: the    */
+/* paper has no gradient).                                                     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t sweeps;     /* adjoint sweeps executed */
+    int converged;      /* 1 if the last sweep changed nothing */
+    int error;          /* EIK_OK or EIK_EDEVICE_TIMEOUT */
+    int64_t launches;   /* kernels enqueued by this call */
+} eik_adjoint_stats;
+
+/* Workspace (bytes, device) needed by eik_dd_adjoint; 0 if invalid (2-D only). */
+size_t eik_dd_adjoint_workspace_size(const eik_grid *grid);
+
+/*
+ * eik_dd_adjoint: dJ/dr for a scalar J(u), at a converged solution u of the
+ * Godunov system of Sec. 1.1 (as returned by eik_fsm, or by eik_dd_solve once
+ * it has converged).  At every reached non-Gamma node j, u_j = F(a_j, r_j)
+ * with a_j the neighbour minima of the branch Alg. 3 takes; the adjoint state
+ * lambda = dJ/du + (dF/du)^T lambda is solved by Gauss-Seidel sweeps in the
+ * 2^d orderings (the system is causal in reverse), and
+ * dJ/dr_j = lambda_j dF_j/dr_j (0 at Gamma and at unreached nodes).  At a tie
+ * (|a-b| = r h exactly, or equal neighbour values) the one-sided derivative of
+ * the branch Alg. 3 selects is used.
+ *   r, gamma, u  [in]  as for eik_fsm; u the forward solution
+ *   dJdu         [in]  dJ/du at every node
+ *   grad_r       [out] dJ/dr at every node
+ *   max_sweeps   cap on the adjoint sweeps
+ *   ws           scratch of eik_dd_adjoint_workspace_size() bytes, 256-byte aligned
+ *   stats        [out] device pointer (may be NULL)
+ */
+int eik_dd_adjoint(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *u, const void *dJdu,
+                   void *grad_r, int64_t max_sweeps, void *ws, size_t ws_bytes, eik_adjoint_stats *stats,
+                   void *stream);
+
 /*
  * eik_dd_solve_noalloc: eik_dd_solve for callers that cannot allocate device
  * memory (for example while a CUDA graph is being captured, or when another

@@ -58,6 +58,11 @@ class DDStats(ctypes.Structure):
                 ("fine_updates", ctypes.c_int64), ("coarse_updates", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
+class AdjointStats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("converged", ctypes.c_int), ("error", ctypes.c_int),
+                ("launches", ctypes.c_int64)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double)]
@@ -88,6 +93,11 @@ def load():
         lib.eik_dd_solve.restype = ctypes.c_int
         lib.eik_dd_solve.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp,
                                      ctypes.c_size_t, vp, vp]
+        lib.eik_dd_adjoint_workspace_size.restype = ctypes.c_size_t
+        lib.eik_dd_adjoint_workspace_size.argtypes = [ctypes.POINTER(Grid)]
+        lib.eik_dd_adjoint.restype = ctypes.c_int
+        lib.eik_dd_adjoint.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, vp, vp, ctypes.c_int64, vp, ctypes.c_size_t,
+                                       vp, vp]
         lib.eik_dd_solve_noalloc.restype = ctypes.c_int
         lib.eik_dd_solve_noalloc.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp, vp]
         lib.eik_profile_enable.restype = ctypes.c_int
@@ -251,6 +261,62 @@ def dd_solve(r, gamma, g, h, tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.
     if s.error:
         raise EikError(s.error, "device-side wait expired")
     return u, _as_dict(s)
+
+
+def eik_dd_adjoint_workspace_size(grid: Grid) -> int:
+    return int(load().eik_dd_adjoint_workspace_size(ctypes.byref(grid)))
+
+
+def eik_dd_adjoint(grid, r, gamma, u, dJdu, grad_r, max_sweeps, ws, stats_dev, stream=None):
+    lib = load()
+    wsp, wsn = _aligned(ws)
+    _check(lib.eik_dd_adjoint(ctypes.byref(grid), _ptr(r), _ptr(gamma), _ptr(u), _ptr(dJdu), _ptr(grad_r),
+                              int(max_sweeps), wsp, wsn, _ptr(stats_dev), _stream(stream)))
+
+
+def adjoint(r, gamma, u, dJdu, h, max_sweeps=100000, stream=None, sync=True):
+    """dJ/dr at the converged solution u for a scalar J with dJ/du given.
+    Returns (grad_r, stats dict)."""
+    _check_like(r, u, dJdu)
+    grid = make_grid(r, h)
+    nbytes = eik_dd_adjoint_workspace_size(grid)
+    if nbytes == 0:
+        raise EikError(-1, eik_last_error())
+    ws = _workspace(nbytes, r.device)
+    grad = torch.empty_like(r)
+    st = torch.zeros(ctypes.sizeof(AdjointStats), dtype=torch.uint8, device=r.device)
+    eik_dd_adjoint(grid, r, gamma.contiguous(), u, dJdu, grad, max_sweeps, ws, st, stream)
+    if not sync:
+        return grad, st
+    s = AdjointStats.from_buffer_copy(bytes(st.cpu().numpy()))
+    if s.error:
+        raise EikError(s.error, "device-side wait expired")
+    return grad, _as_dict(s)
+
+
+class EikonalSolve(torch.autograd.Function):
+    """u = Eikonal solution for slowness r (2-D), differentiable in r.
+
+    forward runs the plain FSM (solver="fsm") or the two-scale DD solve
+    (solver="dd", keyword arguments as for dd_solve) and keeps only the
+    returned u for the backward pass; backward runs eik_dd_adjoint at that u,
+    i.e. it differentiates the converged discrete system."""
+
+    @staticmethod
+    def forward(ctx, r, gamma, g, h, solver="fsm", dd_kwargs=None):
+        if solver == "fsm":
+            u, _ = fsm(r, gamma, g, h)
+        else:
+            u, _ = dd_solve(r, gamma, g, h, **(dd_kwargs or {}))
+        ctx.save_for_backward(r, gamma, u)
+        ctx.h = h
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        r, gamma, u = ctx.saved_tensors
+        grad_r, _ = adjoint(r, gamma, u, grad_u.contiguous(), ctx.h)
+        return grad_r, None, None, None, None, None
 
 
 def parse_dd_stats(st: torch.Tensor) -> dict:

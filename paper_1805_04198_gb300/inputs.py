@@ -141,3 +141,19 @@ def workload_c2(n=257, tiles=8, c=8):
     gamma, g = point_source((n, n, n), (m, m, m))
     return dict(name="c2_3d_%d_pointsrc" % n, r=r, gamma=gamma, g=g, h=h, tiles=(tiles, tiles, tiles), c=c,
                 theta=1.0, max_iter=2 * tiles + 10, tol=0.0)
+
+
+def workload_c4(n=1025, nsrc=64, nrec=256):
+    """Travel-time tomography: 1025^2 (h = 1/1024), true slowness from the
+    Fourier-mode generator (eps = 1/32, seed SEED_C4), starting model the true
+    one Gaussian-smoothed with sigma = eps; sources on x = 0 at rows 16 s + 8,
+    receivers on x = 1 at rows 4 m + 2."""
+    from scipy.ndimage import gaussian_filter
+    h = 1.0 / (n - 1)
+    eps = 1.0 / 32
+    r_true = multiscale_r((n, n), h, SEED_C4, eps)
+    r0 = gaussian_filter(r_true, sigma=eps / h, mode="nearest")
+    src_rows = [16 * s + 8 for s in range(nsrc)]
+    rec_rows = [4 * m + 2 for m in range(nrec)]
+    return dict(name="c4_2d_%d_tomography" % n, r_true=r_true, r0=r0, h=h, src_rows=src_rows,
+                rec_rows=rec_rows, n=n)
