@@ -175,6 +175,61 @@ int eik_dd_adjoint(const eik_grid *grid, const void *r, const uint8_t *gamma, co
                    void *grad_r, int64_t max_sweeps, void *ws, size_t ws_bytes, eik_adjoint_stats *stats,
                    void *stream);
 
+/* ------------------------------------------------------------------------- */
+/* Batched DD: many independent 2-D problems of mixed sizes, each solved by    */
+/* the iteration of eik_dd_solve (Sec. 3.2).  A project addition: the paper     */
+/* solves one problem at a time.                                               */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int fine_queue;     /* Steps 2+3: 0 = one CTA per subdomain; 1 = the CTAs
+                           that fit on the GPU draw subdomains from a queue */
+    int coarse_queue;   /* the same for the shifted coarse grids (Steps 1, 4) */
+    int ctas_per_sm;    /* queue forms: CTAs per SM (0 = as many as fit) */
+    int largest_first;  /* hand out the boxes of the largest problems first */
+} eik_dd_batch_config;
+
+/* Workspace (bytes, device) for eik_dd_solve_batched; 0 if invalid.  The size
+ * does not depend on the configuration. */
+size_t eik_dd_batched_workspace_size(int nprob, const eik_grid *grids, const eik_dd_params *params);
+
+/*
+ * eik_dd_solve_batched: nprob independent problems, problem p being
+ * eik_dd_solve(&grids[p], r[p], gamma[p], g[p], &params[p], u_out[p], ...).
+ * Each problem produces exactly the u_out and statistics of its own
+ * eik_dd_solve call (same arithmetic, same stopping rule on its own max_iter
+ * and tol), except that causal_rounds_max counts the rounds of the batch-wide
+ * causal sweep and `launches` the kernels of the whole batch.
+ *   nprob            1 .. 65535 problems, all 2-D and of one dtype
+ *   grids, params    host arrays [nprob]
+ *   r, gamma, g,     host arrays [nprob] of device pointers, laid out as for
+ *   u_out            eik_dd_solve
+ *   config           host pointer, or NULL for {0, 0, 0, 1}; it changes only
+ *                    the launch shapes, never a result
+ *   ws               scratch of eik_dd_batched_workspace_size() bytes,
+ *                    256-byte aligned, no initialisation needed
+ *   stats            device array [nprob] (may be NULL)
+ * The call only enqueues kernels on `stream` (no allocation, no host
+ * synchronisation, no host<->device copy), so it may be captured into a CUDA
+ * graph; the graph then replays the same problems with the same pointers.
+ * Returns EIK_OK, EIK_EINVAL, EIK_ENOMEM, EIK_ECUDA or EIK_EUNSUPPORTED.
+ */
+int eik_dd_solve_batched(int nprob, const eik_grid *grids, const void *const *r, const uint8_t *const *gamma,
+                         const void *const *g, const eik_dd_params *params, void *const *u_out,
+                         const eik_dd_batch_config *config, void *ws, size_t ws_bytes, eik_dd_stats *stats,
+                         void *stream);
+
+/*
+ * eik_dd_batched_autotune: times eik_dd_solve_batched on this batch under each
+ * candidate configuration (queue or one-CTA-per-box forms of the two box
+ * stages, CTAs per SM, item order), with every problem's max_iter lowered to
+ * min(max_iter, tune_iters), and returns the fastest in *best (host) and its
+ * time in *best_ms (host, may be NULL).  It overwrites u_out and synchronises
+ * the stream after each candidate: call it before capturing a graph.
+ */
+int eik_dd_batched_autotune(int nprob, const eik_grid *grids, const void *const *r, const uint8_t *const *gamma,
+                            const void *const *g, const eik_dd_params *params, void *const *u_out, int tune_iters,
+                            void *ws, size_t ws_bytes, eik_dd_batch_config *best, double *best_ms, void *stream);
+
 /*
  * eik_dd_solve_noalloc: eik_dd_solve for callers that cannot allocate device
  * memory (for example while a CUDA graph is being captured, or when another

@@ -1,0 +1,91 @@
+// dd2_host.cuh -- host-side plan and workspace layout of one 2-D DD problem,
+// shared by the single-problem and the batched solves.
+#pragma once
+
+#include "dd2_device.cuh"
+#include "host_util.h"
+
+namespace eik {
+
+struct DDPlan {
+    DDGeom G;
+    size_t bytes;
+    size_t fine_smem, step1_smem, step4_smem;
+    int grid_threads;
+};
+
+// Checks a DD request (2-D or 3-D); sets the error text and returns false if
+// it is invalid.
+bool dd_validate(const eik_grid *grid, const eik_dd_params *p);
+
+template <class T>
+inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
+    const DDGeom &G = P.G;
+    Carver cv(ws);
+    const size_t ntiles = (size_t)G.tx * G.ty;
+    T *tile_state = cv.take<T>(ntiles * G.tile_elems);
+    T *tile_rsk = cv.take<T>(ntiles * G.tile_sk_elems);
+    T *U = cv.take<T>(G.coarse_elems);
+    T *Uprev = cv.take<T>(G.coarse_elems);
+    T *U0 = cv.take<T>(G.coarse_elems);
+    T *rc = cv.take<T>(G.coarse_elems);
+    T *uk = cv.take<T>(G.coarse_elems);
+    uint8_t *W = cv.take<uint8_t>(G.coarse_elems);
+    uint8_t *wk = cv.take<uint8_t>(G.coarse_elems);
+    T *cu = cv.take<T>(4 * G.coarse_elems);
+    uint8_t *cw = cv.take<uint8_t>(4 * G.coarse_elems);
+    T *rc_sk = cv.take<T>(G.coarse_sk_elems);
+    T *uk_sk = cv.take<T>(G.coarse_sk_elems);
+    T *cold_sk = cv.take<T>(G.coarse_sk_elems);
+    uint8_t *mask_sk = cv.take<uint8_t>(G.coarse_sk_elems);
+    int *done = cv.take<int>(4);
+    double *deltas = cv.take<double>((size_t)max_iter + 2);
+    int *chg = cv.take<int>(4);
+    unsigned *bar = cv.take<unsigned>(4);
+    DevStats *st = cv.take<DevStats>(1);
+    if (A) {
+        A->tile_state = tile_state;
+        A->tile_rsk = tile_rsk;
+        A->U = U;
+        A->Uprev = Uprev;
+        A->U0 = U0;
+        A->rc = rc;
+        A->uk = uk;
+        A->W = W;
+        A->wk = wk;
+        A->cu = cu;
+        A->cw = cw;
+        A->rc_sk = rc_sk;
+        A->uk_sk = uk_sk;
+        A->cold_sk = cold_sk;
+        A->mask_sk = mask_sk;
+        A->done = done;
+        A->deltas = deltas;
+        A->chg = chg;
+        A->bar = bar;
+        A->st = st;
+    }
+    return cv.used + 256;
+}
+
+inline DDPlan dd_plan(const eik_grid *grid, const eik_dd_params *p) {
+    DDPlan P;
+    P.G = make_geom((int)grid->n[0], (int)grid->n[1], p->tiles[0], p->tiles[1], p->coarse_ratio, grid->h);
+    P.step1_smem = P.step4_smem = 0;
+    P.bytes = grid->dtype == EIK_F64 ? dd_layout<double>(P, nullptr, nullptr, p->max_iter)
+                                     : dd_layout<float>(P, nullptr, nullptr, p->max_iter);
+    const int gnb = ceil32(P.G.ncx + 1);
+    P.grid_threads = 32 * gnb;
+    if (grid->dtype == EIK_F64) {
+        P.fine_smem = engine_smem_bytes<double, 1, false>(P.G.tnb, P.G.tny);
+        P.step1_smem = engine_smem_bytes<double, 1, false>(gnb, P.G.ncy + 1);
+        P.step4_smem = engine_smem_bytes<double, 3, true>(gnb, P.G.ncy + 1);
+    } else {
+        P.fine_smem = engine_smem_bytes<float, 1, false>(P.G.tnb, P.G.tny);
+        P.step1_smem = engine_smem_bytes<float, 1, false>(gnb, P.G.ncy + 1);
+        P.step4_smem = engine_smem_bytes<float, 3, true>(gnb, P.G.ncy + 1);
+    }
+    return P;
+}
+
+}  // namespace eik

@@ -6,6 +6,7 @@ no fallback: if libeik.so is missing or cannot be loaded, every call raises.
 
 Entry points mirror the C names:
     eik_fsm_workspace_size, eik_fsm, eik_dd_workspace_size, eik_dd_solve,
+    eik_dd_batched_workspace_size, eik_dd_solve_batched, eik_dd_batched_autotune,
     eik_last_error, eik_version
 plus the conveniences :func:`fsm` and :func:`dd_solve`, which allocate the
 workspace and the output with torch and return host-side statistics.
@@ -63,6 +64,11 @@ class AdjointStats(ctypes.Structure):
                 ("launches", ctypes.c_int64)]
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("fine_queue", ctypes.c_int), ("coarse_queue", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("largest_first", ctypes.c_int)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double)]
@@ -100,6 +106,17 @@ def load():
                                        vp, vp]
         lib.eik_dd_solve_noalloc.restype = ctypes.c_int
         lib.eik_dd_solve_noalloc.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp, vp]
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        lib.eik_dd_batched_workspace_size.restype = ctypes.c_size_t
+        lib.eik_dd_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Grid), ctypes.POINTER(DDParams)]
+        lib.eik_dd_solve_batched.restype = ctypes.c_int
+        lib.eik_dd_solve_batched.argtypes = [ctypes.c_int, ctypes.POINTER(Grid), pp, pp, pp,
+                                             ctypes.POINTER(DDParams), pp, ctypes.POINTER(BatchConfig), vp,
+                                             ctypes.c_size_t, vp, vp]
+        lib.eik_dd_batched_autotune.restype = ctypes.c_int
+        lib.eik_dd_batched_autotune.argtypes = [ctypes.c_int, ctypes.POINTER(Grid), pp, pp, pp,
+                                                ctypes.POINTER(DDParams), pp, ctypes.c_int, vp, ctypes.c_size_t,
+                                                ctypes.POINTER(BatchConfig), ctypes.POINTER(ctypes.c_double), vp]
         lib.eik_profile_enable.restype = ctypes.c_int
         lib.eik_profile_enable.argtypes = [ctypes.c_int]
         lib.eik_profile_collect.restype = ctypes.c_int
@@ -317,6 +334,108 @@ class EikonalSolve(torch.autograd.Function):
         r, gamma, u = ctx.saved_tensors
         grad_r, _ = adjoint(r, gamma, u, grad_u.contiguous(), ctx.h)
         return grad_r, None, None, None, None, None
+
+
+# --------------------------------------------------------------------------
+# Batched DD (many independent 2-D problems)
+# --------------------------------------------------------------------------
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def _struct_array(cls, items):
+    return (cls * len(items))(*items)
+
+
+def eik_dd_batched_workspace_size(grids, params) -> int:
+    n = len(grids)
+    return int(load().eik_dd_batched_workspace_size(n, _struct_array(Grid, grids), _struct_array(DDParams, params)))
+
+
+def eik_dd_solve_batched(grids, r, gamma, g, params, u_out, config, ws, stats_dev, stream=None):
+    """Direct C call; r, gamma, g, u_out are lists of device tensors."""
+    lib = load()
+    wsp, wsn = _aligned(ws)
+    cfg = ctypes.byref(config) if config is not None else None
+    _check(lib.eik_dd_solve_batched(len(grids), _struct_array(Grid, grids), _ptr_array(r), _ptr_array(gamma),
+                                    _ptr_array(g), _struct_array(DDParams, params), _ptr_array(u_out), cfg, wsp, wsn,
+                                    _ptr(stats_dev), _stream(stream)))
+
+
+def eik_dd_batched_autotune(grids, r, gamma, g, params, u_out, tune_iters, ws, stream=None):
+    """Returns (best BatchConfig, its time in ms)."""
+    lib = load()
+    wsp, wsn = _aligned(ws)
+    best = BatchConfig()
+    ms = ctypes.c_double(0.0)
+    _check(lib.eik_dd_batched_autotune(len(grids), _struct_array(Grid, grids), _ptr_array(r), _ptr_array(gamma),
+                                       _ptr_array(g), _struct_array(DDParams, params), _ptr_array(u_out),
+                                       int(tune_iters), wsp, wsn, ctypes.byref(best), ctypes.byref(ms),
+                                       _stream(stream)))
+    return best, ms.value
+
+
+class DDBatch:
+    """A fixed batch of independent 2-D DD problems on one device.
+
+    problems: list of dicts with keys r, gamma, g (device tensors, r and g of
+    one float dtype for the whole batch), h, tiles, coarse_ratio and optionally
+    theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps.  Owns the outputs
+    `u` (list), the workspace and the device statistics.  run() enqueues one
+    batched solve; capture() records it into a CUDA graph that replay() reruns."""
+
+    def __init__(self, problems, config=None):
+        if not problems:
+            raise ValueError("empty batch")
+        self.r = [p["r"] for p in problems]
+        self.gamma = [p["gamma"].contiguous() for p in problems]
+        self.g = [p["g"] for p in problems]
+        for r, gm, g in zip(self.r, self.gamma, self.g):
+            _check_like(r, g)
+            if gm.dtype != torch.uint8 or gm.shape != r.shape:
+                raise ValueError("gamma must be uint8 with r's shape")
+        self.grids = [make_grid(p["r"], p["h"]) for p in problems]
+        self.params = [dd_params(p["tiles"], p["coarse_ratio"], p.get("theta", 1.0), p.get("max_iter", 10),
+                                 p.get("tol", 0.0), p.get("max_fsm_sweeps", 100000), p.get("max_coarse_sweeps", 8))
+                       for p in problems]
+        nbytes = eik_dd_batched_workspace_size(self.grids, self.params)
+        if nbytes == 0:
+            raise EikError(-1, eik_last_error())
+        dev = self.r[0].device
+        self.ws = _workspace(nbytes, dev)
+        self.u = [torch.empty_like(r) for r in self.r]
+        self.stats_dev = torch.zeros(ctypes.sizeof(DDStats) * len(problems), dtype=torch.uint8, device=dev)
+        self.config = config
+        self.graph = None
+
+    def autotune(self, tune_iters=2, stream=None):
+        best, ms = eik_dd_batched_autotune(self.grids, self.r, self.gamma, self.g, self.params, self.u, tune_iters,
+                                           self.ws, stream)
+        self.config = best
+        return best, ms
+
+    def run(self, stream=None):
+        eik_dd_solve_batched(self.grids, self.r, self.gamma, self.g, self.params, self.u, self.config, self.ws,
+                             self.stats_dev, stream)
+
+    def capture(self):
+        """Record one solve into a CUDA graph (warm-up run first)."""
+        self.run()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self.graph
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+
+    def stats(self):
+        raw = bytes(self.stats_dev.cpu().numpy())
+        sz = ctypes.sizeof(DDStats)
+        return [_as_dict(DDStats.from_buffer_copy(raw[i * sz:(i + 1) * sz])) for i in range(len(self.u))]
 
 
 def parse_dd_stats(st: torch.Tensor) -> dict:

@@ -74,12 +74,12 @@ def fourier_field(shape, h, seed, eps, nmodes=32):
     ny, nx = shape
     x = np.arange(nx, dtype=np.float64) * h
     y = np.arange(ny, dtype=np.float64) * h
-    F = np.zeros(shape, dtype=np.float64)
-    for kx, ky, phi in fourier_modes(seed, nmodes, 1.0 / eps, 2.0 / eps):
-        ex = np.exp(1j * (2.0 * math.pi * kx * x))
-        ey = np.exp(1j * (2.0 * math.pi * ky * y + phi))
-        F += np.real(ey[:, None] * ex[None, :])
-    return F
+    modes = fourier_modes(seed, nmodes, 1.0 / eps, 2.0 / eps)
+    # each mode factors as exp(i(2 pi ky y + phi)) exp(i 2 pi kx x); the sum over
+    # modes is then one (ny x nmodes) @ (nmodes x nx) complex product
+    ex = np.stack([np.exp(1j * (2.0 * math.pi * kx * x)) for kx, _, _ in modes])
+    ey = np.stack([np.exp(1j * (2.0 * math.pi * ky * y + phi)) for _, ky, phi in modes])
+    return np.real(ey.T @ ex)
 
 
 def multiscale_r(shape, h, seed, eps, r0_slope=0.3, amp=0.4, floor=0.2):
@@ -141,6 +141,29 @@ def workload_c2(n=257, tiles=8, c=8):
     gamma, g = point_source((n, n, n), (m, m, m))
     return dict(name="c2_3d_%d_pointsrc" % n, r=r, gamma=gamma, g=g, h=h, tiles=(tiles, tiles, tiles), c=c,
                 theta=1.0, max_iter=2 * tiles + 10, tol=0.0)
+
+
+def workload_c3(nprob=256, sides=(257, 513, 1025, 2049), tiles=(8, 16, 32), theta=0.2, seed0=SEED_C3):
+    """Batch of independent 2-D problems.  Problem p draws from SplitMix64(seed0 + p):
+    side n ~ U(sides), subdomains per side T ~ U(tiles), eps ~ U[16h, 64h] with
+    h = 1/(n-1), a seed for its Fourier-mode slowness (as for the 4097^2
+    workload, |k| in [1/eps, 2/eps]) and a point source at a uniformly drawn
+    interior node.  Coarse ratio c = min(8, (n-1)/T); iteration cap 2T + 10."""
+    out = []
+    for p in range(nprob):
+        rng = SplitMix64(seed0 + p)
+        n = sides[rng.randint(0, len(sides) - 1)]
+        T = tiles[rng.randint(0, len(tiles) - 1)]
+        h = 1.0 / (n - 1)
+        eps = h * (16.0 + 48.0 * rng.uniform())
+        fseed = rng.next_u64()
+        sy, sx = rng.randint(1, n - 2), rng.randint(1, n - 2)
+        r = multiscale_r((n, n), h, fseed, eps)
+        gamma, g = point_source((n, n), (sy, sx))
+        S = (n - 1) // T
+        out.append(dict(name="c3_p%d_%d_T%d" % (p, n, T), r=r, gamma=gamma, g=g, h=h, tiles=(T, T),
+                        c=min(8, S), theta=theta, max_iter=2 * T + 10, tol=0.0))
+    return out
 
 
 def workload_c4(n=1025, nsrc=64, nrec=256):
