@@ -149,7 +149,8 @@ __device__ __forceinline__ T local_solve3(const T *vm, const T *vp, T rh, uint8_
 constexpr int DEV_OK = 0;
 constexpr int DEV_TIMEOUT = -4;
 
-// Bounded spin limit for every device-side wait (iterations of ~64 ns sleep).
+// Bounded spin limit for every device-side wait (iterations of at most ~1 us
+// sleep each, so an expired wait reports within seconds).
 constexpr long long SPIN_LIMIT = 1ll << 22;
 
 // Grid-wide barrier for cooperative launches (all CTAs co-resident).  bar[0]

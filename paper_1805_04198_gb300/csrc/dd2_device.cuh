@@ -321,13 +321,138 @@ __device__ bool causal_line(const DDArgs<T> &A, bool horizontal, int line, int r
     return __any_sync(FULL, changed);  // warp-uniform: any lane raised a node
 }
 
+// The same sweep with the whole line staged in shared memory: one warp per
+// line, values su[] and per-node bytes sw[] (bit 0: wind along +axis, bit 1:
+// along -axis, bit 2: linked to its scan predecessor in the current pass,
+// bit 7: raised).  In a pass each lane scans a contiguous segment of
+// ceil(len/32) nodes serially, the lanes' segment results are combined by one
+// warp scan of (value, linked-throughout) pairs, and each lane raises the
+// linked prefix of its segment to the carry that reaches it.  The segmented
+// max-scan has one result, so the values equal those of causal_line.
+__host__ __device__ inline size_t causal_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 template <class T>
-__global__ void k_causal(DDArgs<T> A, int only_if_not_done) {
+__host__ __device__ inline size_t causal_warp_bytes(int lw) {
+    return causal_align16((size_t)lw * sizeof(T)) + causal_align16((size_t)lw);
+}
+
+template <class T>
+__device__ void causal_pass_smem(T *su, uint8_t *sw, int len, int rev) {
+    const T INF = Num<T>::inf();
+    const int lane = threadIdx.x & 31;
+    const int seg = (len + 31) >> 5;
+    const int s = lane * seg;
+    const int e = s + seg < len ? s + seg : len;
+    const uint8_t dirbit = rev ? 2 : 1;
+    // original value of the node before this segment in scan order
+    T prev_orig = (s > 0 && s <= len) ? su[rev ? len - s : s - 1] : INF;
+    __syncwarp();
+    T vprev = -INF;
+    bool through = true;
+    for (int pos = s; pos < e; ++pos) {
+        const int idx = rev ? len - 1 - pos : pos;
+        const T orig = su[idx];
+        uint8_t w = sw[idx];
+        const bool f = (w & dirbit) && pos > 0 && (prev_orig < INF);
+        const T v = (pos > s && f) ? fmax(orig, vprev) : orig;
+        through = through && f;
+        w = f ? (uint8_t)(w | 4) : (uint8_t)(w & ~4);
+        if (v > orig) {
+            su[idx] = v;
+            w |= 0x80;
+        }
+        sw[idx] = w;
+        prev_orig = orig;
+        vprev = v;
+    }
+    // carry reaching each segment: composition of x -> (all ? max(v, x) : v)
+    T cv = vprev;
+    bool ca = through;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T pv = __shfl_up_sync(FULL, cv, o);
+        const bool pa = __shfl_up_sync(FULL, ca ? 1 : 0, o) != 0;
+        if (lane >= o) {
+            cv = ca ? fmax(cv, pv) : cv;
+            ca = ca && pa;
+        }
+    }
+    T carry = __shfl_up_sync(FULL, cv, 1);
+    if (lane == 0) carry = -INF;
+    if (carry > -INF) {
+        for (int pos = s; pos < e; ++pos) {
+            const int idx = rev ? len - 1 - pos : pos;
+            const uint8_t w = sw[idx];
+            if (!(w & 4)) break;
+            if (carry > su[idx]) {
+                su[idx] = carry;
+                sw[idx] = (uint8_t)(w | 0x80);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Both passes of Alg. 2 on one coarse line through shared memory; returns
+// whether any node was raised (warp-uniform).
+template <class T>
+__device__ bool causal_line_smem(const DDArgs<T> &A, bool horizontal, int line, T *su, uint8_t *sw) {
+    const DDGeom &G = A.G;
+    const int lane = threadIdx.x & 31;
+    const int len = horizontal ? G.nx : G.ny;
+    const int fixedc = line * G.c;
+    const int axis = horizontal ? 0 : 1;
+    constexpr int UNR = 4;
+    for (int p0 = 0; p0 < len; p0 += 32 * UNR) {
+        T uv[UNR];
+        uint8_t wv[UNR];
+#pragma unroll
+        for (int r = 0; r < UNR; ++r) {
+            const int p = p0 + 32 * r + lane;
+            uv[r] = Num<T>::inf();
+            wv[r] = WIND_ZERO;
+            if (p < len) {
+                const size_t a = coarse_addr(G, horizontal ? p : fixedc, horizontal ? fixedc : p);
+                uv[r] = __ldcg(A.U + a);
+                wv[r] = __ldcg(A.W + a);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < UNR; ++r) {
+            const int p = p0 + 32 * r + lane;
+            if (p < len) {
+                const int wc = wind_comp(wv[r], axis);
+                su[p] = uv[r];
+                sw[p] = (uint8_t)((wc > 0 ? 1 : 0) | (wc < 0 ? 2 : 0));
+            }
+        }
+    }
+    __syncwarp();
+    causal_pass_smem(su, sw, len, 0);
+    causal_pass_smem(su, sw, len, 1);
+    bool changed = false;
+    for (int p = lane; p < len; p += 32) {
+        if (sw[p] & 0x80) {
+            A.U[coarse_addr(G, horizontal ? p : fixedc, horizontal ? fixedc : p)] = su[p];
+            changed = true;
+        }
+    }
+    __syncwarp();
+    return __any_sync(FULL, changed);
+}
+
+// lw > 0: lines staged in shared memory (lw = capacity per warp, dynamic
+// shared memory of causal_warp_bytes<T>(lw) per warp); lw = 0: lines read
+// and written in place, 32 nodes at a time.
+template <class T>
+__global__ void k_causal(DDArgs<T> A, int only_if_not_done, int lw) {
     if (only_if_not_done && *A.done) return;
     const DDGeom &G = A.G;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    extern __shared__ __align__(16) unsigned char causal_smem[];
+    T *su = reinterpret_cast<T *>(causal_smem + (size_t)(threadIdx.x >> 5) * causal_warp_bytes<T>(lw));
+    uint8_t *sw = reinterpret_cast<uint8_t *>(su) + causal_align16((size_t)lw * sizeof(T));
     __shared__ int blk_changed;
     if (blockIdx.x == 0 && threadIdx.x < 3) A.chg[threadIdx.x] = 0;
     if (!grid_barrier(A.bar, &A.st->err)) return;
@@ -337,13 +462,21 @@ __global__ void k_causal(DDArgs<T> A, int only_if_not_done) {
         __syncthreads();
         bool ch = false;
         for (int l = gw; l <= G.ncy; l += warps_total) {
-            ch |= causal_line(A, true, l, 0);
-            ch |= causal_line(A, true, l, 1);
+            if (lw > 0) {
+                ch |= causal_line_smem(A, true, l, su, sw);
+            } else {
+                ch |= causal_line(A, true, l, 0);
+                ch |= causal_line(A, true, l, 1);
+            }
         }
         if (!grid_barrier(A.bar, &A.st->err)) return;
         for (int l = gw; l <= G.ncx; l += warps_total) {
-            ch |= causal_line(A, false, l, 0);
-            ch |= causal_line(A, false, l, 1);
+            if (lw > 0) {
+                ch |= causal_line_smem(A, false, l, su, sw);
+            } else {
+                ch |= causal_line(A, false, l, 0);
+                ch |= causal_line(A, false, l, 1);
+            }
         }
         if (lane == 0 && ch) atomicOr(&blk_changed, 1);
         __syncthreads();

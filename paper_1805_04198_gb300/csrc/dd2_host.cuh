@@ -5,6 +5,8 @@
 #include "dd2_device.cuh"
 #include "host_util.h"
 
+#include <algorithm>
+
 namespace eik {
 
 struct DDPlan {
@@ -66,6 +68,43 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
         A->st = st;
     }
     return cv.used + 256;
+}
+
+// Launch shape of a cooperative causal-sweep kernel: lines staged in shared
+// memory (one warp per line, up to 8 warps per CTA) when a line of lw nodes
+// fits, else the in-place form with 8 warps per CTA.  blocks is capped by what
+// is co-resident so that the grid barrier cannot wait on an unscheduled CTA.
+struct CausalShape {
+    int threads, blocks, lw;
+    size_t smem;
+};
+
+template <class T>
+inline int causal_shape(const void *kernel, int lw, int lines, int nsm, int smem_optin, CausalShape &cs) {
+    const size_t wb = causal_warp_bytes<T>(lw);
+    int wpb = (int)std::min<size_t>(8, (size_t)std::max(0, smem_optin - 1024) / wb);
+    if (wpb >= 1) {
+        cs.threads = 32 * wpb;
+        cs.smem = (size_t)wpb * wb;
+        cs.lw = lw;
+    } else {
+        wpb = 8;
+        cs.threads = 256;
+        cs.smem = 0;
+        cs.lw = 0;
+    }
+    int rc = cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs.smem),
+                        "smem attr causal");
+    if (rc) return rc;
+    int per_sm = 0;
+    rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, cs.threads, cs.smem), "occupancy");
+    if (rc) return rc;
+    if (per_sm < 1) {
+        set_error("causal sweep: no CTA of %d threads and %zu bytes fits on an SM", cs.threads, cs.smem);
+        return EIK_EUNSUPPORTED;
+    }
+    cs.blocks = std::max(1, std::min(per_sm * nsm, (lines + wpb - 1) / wpb));
+    return EIK_OK;
 }
 
 inline DDPlan dd_plan(const eik_grid *grid, const eik_dd_params *p) {

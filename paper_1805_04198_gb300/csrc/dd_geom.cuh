@@ -21,6 +21,7 @@ struct DDGeom {
     int tx, ty;        // subdomains per axis
     int sx, sy;        // cells per subdomain
     int c;             // coarse ratio
+    int cshift;        // log2(c) when c is a power of two, else -1
     int ncx, ncy;      // (nx-1)/c, (ny-1)/c
     int ngrids;        // 2c - 1
     // tile boxes
@@ -59,6 +60,9 @@ __host__ __device__ inline GridDesc grid_desc(const DDGeom &G, int g) {
 __host__ inline DDGeom make_geom(int nx, int ny, int tx, int ty, int c, double h) {
     DDGeom G;
     G.nx = nx; G.ny = ny; G.tx = tx; G.ty = ty; G.c = c;
+    G.cshift = -1;
+    for (int sft = 0; sft < 31; ++sft)
+        if ((1 << sft) == c) G.cshift = sft;
     G.sx = (nx - 1) / tx; G.sy = (ny - 1) / ty;
     G.ncx = (nx - 1) / c; G.ncy = (ny - 1) / c;
     G.ngrids = 2 * c - 1;
@@ -83,7 +87,8 @@ __host__ inline DDGeom make_geom(int nx, int ny, int tx, int ty, int c, double h
 
 // Shifted grid and in-grid indices (i, j) of a coarse-set fine node (X, Y).
 __host__ __device__ inline void coarse_locate(const DDGeom &G, int X, int Y, int &g, int &i, int &j) {
-    int rx = X % G.c, ry = Y % G.c;
+    const bool p2 = G.cshift >= 0;
+    const int rx = p2 ? (X & (G.c - 1)) : X % G.c, ry = p2 ? (Y & (G.c - 1)) : Y % G.c;
     if (rx == 0 && ry == 0) {
         g = 0;
     } else if (ry == 0) {
@@ -91,8 +96,8 @@ __host__ __device__ inline void coarse_locate(const DDGeom &G, int X, int Y, int
     } else {
         g = G.c - 1 + ry;
     }
-    i = X / G.c;
-    j = Y / G.c;
+    i = p2 ? X >> G.cshift : X / G.c;
+    j = p2 ? Y >> G.cshift : Y / G.c;
 }
 
 __host__ __device__ inline size_t coarse_addr(const DDGeom &G, int X, int Y) {
@@ -103,6 +108,7 @@ __host__ __device__ inline size_t coarse_addr(const DDGeom &G, int X, int Y) {
 }
 
 __host__ __device__ inline bool in_coarse_set(const DDGeom &G, int X, int Y) {
+    if (G.cshift >= 0) return ((X & (G.c - 1)) == 0) || ((Y & (G.c - 1)) == 0);
     return (X % G.c == 0) || (Y % G.c == 0);
 }
 

@@ -161,14 +161,10 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
                          "smem attr step4")))
         return rc;
     // causal sweep: cooperative grid sized to what is co-resident
-    const int causal_threads = 256;
-    int per_sm = 0;
-    if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_causal<T>, causal_threads, 0),
-                         "occupancy")))
+    CausalShape cs;
+    if ((rc = causal_shape<T>((const void *)k_causal<T>, std::max(G.nx, G.ny), std::max(G.ncx, G.ncy) + 1, nsm,
+                              smem_optin, cs)))
         return rc;
-    const int lines = std::max(G.ncx, G.ncy) + 1;
-    int causal_blocks = std::min(per_sm * nsm, std::max(1, (lines + 7) / 8));
-    if (causal_blocks < 1) causal_blocks = 1;
 
     const int ew = 256;
     const int eb = (int)std::min<size_t>((G.coarse_elems + ew - 1) / ew, (size_t)nsm * 8);
@@ -181,9 +177,9 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     EIK_LAUNCH("dd_pack_coarse", s, k_pack_coarse<T><<<eb, ew, 0, s>>>(A)); ++nl;
     EIK_LAUNCH("dd_step1_coarse_fsm", s, DDKernels<T>::step1<<<G.ngrids, P.grid_threads, P.step1_smem, s>>>(A)); ++nl;
     auto launch_causal = [&](int only) -> int {
-        void *args[] = {&A, &only};
+        void *args[] = {&A, &only, &cs.lw};
         int tok = prof_begin("dd_causal_sweep", s);
-        int r2 = cuda_check(cudaLaunchCooperativeKernel((void *)k_causal<T>, causal_blocks, causal_threads, args, 0, s),
+        int r2 = cuda_check(cudaLaunchCooperativeKernel((void *)k_causal<T>, cs.blocks, cs.threads, args, cs.smem, s),
                             "causal launch");
         prof_end(tok, s);
         ++nl;

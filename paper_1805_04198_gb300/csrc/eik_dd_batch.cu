@@ -183,10 +183,14 @@ __global__ void kb_finalize(const DDArgs<T> *__restrict__ args, BatchCtl C, eik_
 // rounds as the single-problem kernel, with the lines of all problems dealt to
 // the warps of one cooperative grid.
 template <class T>
-__global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, BatchCtl C, int only_if_not_done) {
+__global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, BatchCtl C, int only_if_not_done,
+                          int lw) {
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    extern __shared__ __align__(16) unsigned char causal_smem[];
+    T *su = reinterpret_cast<T *>(causal_smem + (size_t)(threadIdx.x >> 5) * causal_warp_bytes<T>(lw));
+    uint8_t *sw = reinterpret_cast<uint8_t *>(su) + causal_align16((size_t)lw * sizeof(T));
     __shared__ int blk_changed;
     if (blockIdx.x == 0 && threadIdx.x < 3) C.chg[threadIdx.x] = 0;
     if (!grid_barrier(C.bar, C.err)) return;
@@ -199,16 +203,24 @@ __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, 
             int local;
             const DDArgs<T> &A = args[seg_find(hl.pre, hl.n, l, local)];
             if (only_if_not_done && *A.done) continue;
-            ch |= causal_line(A, true, local, 0);
-            ch |= causal_line(A, true, local, 1);
+            if (lw > 0) {
+                ch |= causal_line_smem(A, true, local, su, sw);
+            } else {
+                ch |= causal_line(A, true, local, 0);
+                ch |= causal_line(A, true, local, 1);
+            }
         }
         if (!grid_barrier(C.bar, C.err)) return;
         for (int l = gw; l < vl.total; l += warps_total) {
             int local;
             const DDArgs<T> &A = args[seg_find(vl.pre, vl.n, l, local)];
             if (only_if_not_done && *A.done) continue;
-            ch |= causal_line(A, false, local, 0);
-            ch |= causal_line(A, false, local, 1);
+            if (lw > 0) {
+                ch |= causal_line_smem(A, false, local, su, sw);
+            } else {
+                ch |= causal_line(A, false, local, 0);
+                ch |= causal_line(A, false, local, 1);
+            }
         }
         if (lane == 0 && ch) atomicOr(&blk_changed, 1);
         __syncthreads();
@@ -501,13 +513,12 @@ static int batch_run(int nprob, const eik_grid *grids, const void *const *r, con
     const bool fq = cfg.fine_queue != 0, gq = cfg.coarse_queue != 0;
 
     // causal sweep: cooperative grid of what is co-resident
-    const int causal_threads = 256;
-    int per_sm = 0;
-    if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_causal<T>, causal_threads, 0),
-                         "occupancy")))
+    int maxlen = 0;
+    for (int p = 0; p < nprob; ++p) maxlen = std::max(maxlen, std::max(B.P[p].G.nx, B.P[p].G.ny));
+    CausalShape cs;
+    if ((rc = causal_shape<T>((const void *)kb_causal<T>, maxlen, std::max(B.hl_total, B.vl_total), nsm, smem_optin,
+                              cs)))
         return rc;
-    const int lines = std::max(B.hl_total, B.vl_total);
-    const int causal_blocks = std::max(1, std::min(per_sm * nsm, (lines + 7) / 8));
     Segs tiles{dtab + B.tiles_at, nprob, B.tiles_total};
     Segs coarse{dtab + B.coarse_at, nprob, B.coarse_total};
     Segs hl{dtab + B.hl_at, nprob, B.hl_total};
@@ -528,9 +539,9 @@ static int batch_run(int nprob, const eik_grid *grids, const void *const *r, con
         ++nl;
     }
     auto launch_causal = [&](int only) -> int {
-        void *kargs[] = {(void *)&dargs, &hl, &vl, &C, &only};
+        void *kargs[] = {(void *)&dargs, &hl, &vl, &C, &only, &cs.lw};
         int tok = prof_begin("dd_causal_sweep", s);
-        int r2 = cuda_check(cudaLaunchCooperativeKernel((void *)kb_causal<T>, causal_blocks, causal_threads, kargs, 0, s),
+        int r2 = cuda_check(cudaLaunchCooperativeKernel((void *)kb_causal<T>, cs.blocks, cs.threads, kargs, cs.smem, s),
                             "causal launch");
         prof_end(tok, s);
         ++nl;

@@ -83,6 +83,7 @@ def _dd_case(n, tiles, c, amp=0.5, eps=0.25, src=None):
     (65, (2, 4), 8, 1.0, 3),      # theta = 1, anisotropic tiling
     (97, (3, 3), 16, 0.2, 5),     # 33-node subdomains: two blocks, ragged tail
     (129, (2, 2), 8, 0.3, 4),     # 65-node subdomains, c < S
+    (73, (3, 3), 6, 0.2, 3),      # coarse ratio not a power of two
 ])
 def test_dd_fp64_bitwise(gpu, n, tiles, c, theta, kmax):
     r, gamma, g, h = _dd_case(n, tiles, c)
