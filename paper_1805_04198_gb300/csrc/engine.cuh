@@ -317,40 +317,6 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
         hal = halo[(s0 - lane) & (RROWS - 1)];
         const T *sbase = sring + (size_t)((J % SRCH) * CH) * 32 + lane;
         const uint8_t *bbase = sbring + ((J % SRCH) * CH) * 32 + lane;
-        // Interior chunk: every lane's rows of these 8 steps (s0-31 .. s0+7) and
-        // the rows read ahead (up to s0+9) lie inside the box, so no row test is
-        // needed.  hcur is +inf without a predecessor block and the halo is +inf
-        // without a successor column, so lanes 0 and 31 take them unguarded.
-        if (s0 >= 32 && s0 + CH + 2 <= NY) {
-            const int q0 = s0 - lane;  // logical row of step 0 of this chunk
-#pragma unroll
-            for (int i = 0; i < CH; ++i) {
-                const int m = q0 + i;
-                const T dn2 = myring[((m + 2) & (RROWS - 1)) * 32];
-                const T hal2 = halo[(m + 1) & (RROWS - 1)];
-                T sv[NST > 0 ? NST : 1];
-#pragma unroll
-                for (int kk = 0; kk < NST; ++kk) sv[kk] = sbase[((size_t)kk * SRCH * CH + i) * 32];
-                const uint8_t sbv = HASB ? bbase[i * 32] : (uint8_t)0;
-                const T hin = __shfl_sync(FULL, hcur, i);
-                const T fromleft = __shfl_up_sync(FULL, last, 1);
-                const T fromright = __shfl_down_sync(FULL, dnx, 1);
-                const T left = lane0 ? hin : fromleft;
-                const T right = lane31 ? hal : fromright;
-                bool ch = false;
-                const T upd = pol.update(cur, SX > 0 ? left : right, SX > 0 ? right : left, SY > 0 ? last : dnx,
-                                         SY > 0 ? dnx : last, sv, sbv, ch);
-                const T nw = colok ? upd : INF;
-                changed = changed || (colok && ch);
-                myring[(m & (RROWS - 1)) * 32] = nw;
-                if (lane31 && has_next) hand[m] = nw;
-                last = nw;
-                cur = dnx;
-                dnx = colok ? dn2 : INF;
-                hal = hal2;
-            }
-            continue;
-        }
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
             const int m = s0 + i - lane;
