@@ -176,6 +176,66 @@ def test_fsm_full_size_fp32_against_oracle(gpu):
     assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
 
 
+# The DD workload of the benchmark: 4097^2, 16x16 subdomains, coarse ratio 16,
+# theta 0.2, FP32, in the launch configuration bench.py times.
+C1_DD = dict(theta=0.2, tol=1e-6, max_coarse_sweeps=8)
+
+
+def _godunov_2d(vmx, vpx, vmy, vpy, rh):
+    """Godunov local solve (Sec. 1.1, eq. godonuv) written out in numpy, FP64."""
+    a = np.minimum(vmx, vpx)
+    b = np.minimum(vmy, vpy)
+    with np.errstate(invalid="ignore"):
+        d = a - b
+        two = (a + b + np.sqrt(np.maximum(2.0 * rh * rh - d * d, 0.0))) / 2.0
+        one = np.minimum(a, b) + rh
+        return np.where(np.abs(d) < rh, two, one)
+
+
+def test_dd_full_size_first_pass_against_oracle(gpu):
+    """4097^2 DD stopped after Step 1, the causal sweep and one pass of
+    subdomain solves with Alg. 4 (max_iter = 0), FP32 on the GPU against the
+    FP64 oracle on the same rounded slowness, every node."""
+    w = I.workload_c1()
+    r32 = w["r"].astype(np.float32)
+    u_ref, s_ref, _ = O.dd(r32.astype(np.float64), w["gamma"], w["g"], w["h"], w["tiles"], w["c"], max_iter=0,
+                           **C1_DD)
+    u, st = gpu.dd_solve(_t(r32, torch.float32), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float32), w["h"],
+                         w["tiles"], w["c"], max_iter=0, **C1_DD)
+    assert st["iters"] == s_ref["iters"] == 0 and st["error"] == 0
+    assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
+
+
+def test_dd_full_size_fixed_point_property(gpu):
+    """4097^2 DD after the benchmark's 42 iterations.  Every subdomain solve
+    ends at its Gauss-Seidel fixed point, so at each node strictly inside a
+    subdomain (neighbours included, so that no neighbour took another
+    subdomain's value in Alg. 4) u equals the Godunov local solve of its four
+    neighbours, up to FP32 rounding.  Checked at every such node."""
+    w = I.workload_c1()
+    r32 = w["r"].astype(np.float32)
+    u, st = gpu.dd_solve(_t(r32, torch.float32), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float32), w["h"],
+                         w["tiles"], w["c"], max_iter=w["max_iter"], **C1_DD)
+    assert st["iters"] == w["max_iter"] and st["error"] == 0 and st["fsm_cap_hits"] == 0
+    U = u.cpu().numpy().astype(np.float64)
+    n = U.shape[0]
+    S = (n - 1) // w["tiles"][0]
+    loc = np.arange(n) % S
+    inner = (loc >= 2) & (loc <= S - 2)
+    mask = inner[:, None] & inner[None, :] & (w["gamma"] == 0)
+    rh = r32.astype(np.float64) * w["h"]
+    inf = np.full((n, 1), np.inf)
+    vmx = np.hstack([inf, U[:, :-1]])
+    vpx = np.hstack([U[:, 1:], inf])
+    vmy = np.vstack([inf.T, U[:-1, :]])
+    vpy = np.vstack([U[1:, :], inf.T])
+    ls = _godunov_2d(vmx, vpx, vmy, vpy, rh)
+    m = mask & np.isfinite(U)
+    assert m.sum() > 0.9 * mask.sum()
+    rel = np.abs(U[m] - ls[m]) / np.abs(U[m])
+    assert rel.max() <= TOL32
+
+
 def _dd3_case(n, amp=0.4, eps=0.25, src=None):
     h = 1.0 / (n - 1)
     r = I.sin_product((n, n, n), h, amp, eps)
