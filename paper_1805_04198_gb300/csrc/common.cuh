@@ -98,50 +98,38 @@ __device__ __forceinline__ T local_solve2_value(T vmx, T vpx, T vmy, T vpy, T rh
 // smallest, else the three-term quadratic written in t = u - a_p0:
 //   t^2 + (t - d1)^2 + (t - d2)^2 = (r h)^2.
 // The wind has the per-axis sign of Alg. 3 on the axes used.  With a_p2 = inf
-// it reduces exactly to local_solve2.
+// it reduces exactly to local_solve2.  The sort is done by ranks and selects
+// (no indexed local arrays); the arithmetic is the same sequence of rounded
+// operations on the sorted values.
 template <class T>
 __device__ __forceinline__ T local_solve3(const T *vm, const T *vp, T rh, uint8_t &wind) {
     using N = Num<T>;
-    T a[3];
-    int s[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const bool lm = vm[k] < vp[k];
-        a[k] = lm ? vm[k] : vp[k];
-        s[k] = lm ? 1 : -1;
+    const bool l0 = vm[0] < vp[0], l1 = vm[1] < vp[1], l2 = vm[2] < vp[2];
+    const T a0 = l0 ? vm[0] : vp[0], a1 = l1 ? vm[1] : vp[1], a2 = l2 ? vm[2] : vp[2];
+    // stable ranks: axis b precedes axis c when a_b < a_c, or a_b == a_c and b < c
+    const int r0 = (a1 < a0 ? 1 : 0) + (a2 < a0 ? 1 : 0);
+    const int r1 = (a0 <= a1 ? 1 : 0) + (a2 < a1 ? 1 : 0);
+    const int r2 = (a0 <= a2 ? 1 : 0) + (a1 <= a2 ? 1 : 0);
+    const T v0 = r0 == 0 ? a0 : (r1 == 0 ? a1 : a2);
+    const T v1 = r0 == 1 ? a0 : (r1 == 1 ? a1 : a2);
+    const T v2 = r0 == 2 ? a0 : (r1 == 2 ? a1 : a2);
+    const T d01 = N::sub(v0, v1);
+    const bool two = fabs(d01) < rh;
+    const T disc = N::sub(N::mul(N::mul(T(2), rh), rh), N::mul(d01, d01));
+    const T u2 = N::mul(N::add(N::add(v0, v1), N::sqrt_solve(fmax(disc, T(0)))), T(0.5));
+    const T u1 = N::add(v0, rh);
+    const bool three = two && (u2 > v2);
+    T u = two ? u2 : u1;
+    if (three) {
+        const T d1 = N::sub(v1, v0);
+        const T d2 = N::sub(v2, v0);
+        const T sd = N::add(d1, d2);
+        T disc3 = N::sub(N::mul(sd, sd), N::mul(T(3), N::sub(N::add(N::mul(d1, d1), N::mul(d2, d2)), N::mul(rh, rh))));
+        if (disc3 < T(0)) disc3 = T(0);
+        u = N::add(v0, N::div(N::add(sd, N::sqrt_solve(disc3)), T(3)));
     }
-    int p0 = 0, p1 = 1, p2 = 2, t;
-    if (a[p1] < a[p0]) { t = p0; p0 = p1; p1 = t; }
-    if (a[p2] < a[p1]) {
-        t = p1; p1 = p2; p2 = t;
-        if (a[p1] < a[p0]) { t = p0; p0 = p1; p1 = t; }
-    }
-    int w[3] = {0, 0, 0};
-    T u;
-    const T d01 = N::sub(a[p0], a[p1]);
-    if (fabs(d01) < rh) {
-        const T disc = N::sub(N::mul(N::mul(T(2), rh), rh), N::mul(d01, d01));
-        u = N::mul(N::add(N::add(a[p0], a[p1]), N::sqrt_solve(fmax(disc, T(0)))), T(0.5));
-        if (u > a[p2]) {
-            const T d1 = N::sub(a[p1], a[p0]);
-            const T d2 = N::sub(a[p2], a[p0]);
-            const T sd = N::add(d1, d2);
-            T disc3 = N::sub(N::mul(sd, sd),
-                             N::mul(T(3), N::sub(N::add(N::mul(d1, d1), N::mul(d2, d2)), N::mul(rh, rh))));
-            if (disc3 < T(0)) disc3 = T(0);
-            u = N::add(a[p0], N::div(N::add(sd, N::sqrt_solve(disc3)), T(3)));
-            w[0] = s[0];
-            w[1] = s[1];
-            w[2] = s[2];
-        } else {
-            w[p0] = s[p0];
-            w[p1] = s[p1];
-        }
-    } else {
-        u = N::add(a[p0], rh);
-        if (u < N::inf()) w[p0] = s[p0];
-    }
-    wind = wind_pack(w[0], w[1], w[2]);
+    const int nt = three ? 3 : (two ? 2 : (u < N::inf() ? 1 : 0));  // axes used, by rank
+    wind = wind_pack(r0 < nt ? (l0 ? 1 : -1) : 0, r1 < nt ? (l1 ? 1 : -1) : 0, r2 < nt ? (l2 ? 1 : -1) : 0);
     return u;
 }
 

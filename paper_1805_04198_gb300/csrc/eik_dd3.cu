@@ -83,46 +83,128 @@ __device__ __forceinline__ int coarse_axes3(int X, int Y, int Z, int c) {
 // --------------------------------------------------------------------------
 // Box sweeps in shared memory along hyperplanes.  Sweep k uses ordering
 // k mod 8 of the paper's loop nest: sign of x = bit 2, y = bit 1, z = bit 0.
-// The update functor returns the new value of a node from its neighbours.
+// Thread t owns the columns (x, y) = c mod mx, c / mx for c = t, t + blockDim,
+// ...; hyperplane i + j + k = dg (logical indices of the ordering) holds one
+// node of each column, so a thread updates at most one node per owned column
+// per hyperplane.  The per-node read-only data the policy needs ("statics",
+// from global memory) are loaded one hyperplane ahead into registers, so their
+// latency overlaps the current hyperplane and its barrier.  The policy gives
+// load(x, y, z, idx) -> Stat and apply(self, vm, vp, stat, idx, changed).
 // --------------------------------------------------------------------------
+constexpr int BOX3_COLS = 4;       // columns per thread with prefetched statics
+constexpr int BOX3_THREADS = 512;  // threads of a box-sweep CTA
+
+// Shared-memory plane stride of a box: the x-y plane padded to an even number
+// of elements.  Along a hyperplane, neighbouring columns' nodes are one plane
+// apart in z and one element apart in x (or y), so with an odd plane size
+// (e.g. 33 x 33) a warp's accesses would all fall into one bank.
+__host__ __device__ inline int box3_ps(int mx, int my) { return mx * my + ((mx * my) & 1); }
+
 template <class T, class P>
 __device__ void box3_sweeps(T *su, int mx, int my, int mz, const P &pol, long long max_sweeps, long long &sweeps,
                             bool &conv) {
+    using S = typename P::Stat;
     const T INF = Num<T>::inf();
     const int ndiag = mx + my + mz - 2;
+    const int ncol = mx * my;
+    const int plane = box3_ps(mx, my);
+    int cx[BOX3_COLS], cy[BOX3_COLS];
+#pragma unroll
+    for (int t = 0; t < BOX3_COLS; ++t) {
+        const int c = threadIdx.x + t * blockDim.x;
+        cx[t] = c < ncol ? c % mx : 0;
+        cy[t] = c < ncol ? c / mx : 0;
+    }
+    // one node: gather neighbours from shared memory and apply the policy
+    auto node = [&](int x, int y, int z, S st, bool &ch) {
+        const int idx = z * plane + y * mx + x;
+        T vm[3], vp[3];
+        vm[0] = x > 0 ? su[idx - 1] : INF;
+        vp[0] = x + 1 < mx ? su[idx + 1] : INF;
+        vm[1] = y > 0 ? su[idx - mx] : INF;
+        vp[1] = y + 1 < my ? su[idx + mx] : INF;
+        vm[2] = z > 0 ? su[idx - plane] : INF;
+        vp[2] = z + 1 < mz ? su[idx + plane] : INF;
+        const T self = su[idx];
+        S sl = st;
+        pol.fill(sl, idx);
+        bool c1 = false;
+        const T nw = pol.apply(self, vm, vp, sl, idx, c1);
+        if (c1) {
+            su[idx] = nw;
+            ch = true;
+        }
+    };
     sweeps = 0;
     conv = false;
     for (long long k = 0; k < max_sweeps; ++k) {
         const int q = (int)(k & 7);
         const int sx = (q & 4) ? 1 : -1, sy = (q & 2) ? 1 : -1, sz = (q & 1) ? 1 : -1;
+        int base[BOX3_COLS];  // logical x + y of each owned column (kp = dg - base)
+#pragma unroll
+        for (int t = 0; t < BOX3_COLS; ++t) {
+            const int c = threadIdx.x + t * blockDim.x;
+            base[t] = c < ncol ? (sx > 0 ? cx[t] : mx - 1 - cx[t]) + (sy > 0 ? cy[t] : my - 1 - cy[t]) : -(1 << 28);
+        }
+        auto zof = [&](int kp) { return sz > 0 ? kp : mz - 1 - kp; };
+        S cur[BOX3_COLS], nxt[BOX3_COLS];
+#pragma unroll
+        for (int t = 0; t < BOX3_COLS; ++t) {
+            const int kp = 0 - base[t];
+            if (kp >= 0 && kp < mz) cur[t] = pol.load(cx[t], cy[t], zof(kp), (zof(kp) * my + cy[t]) * mx + cx[t]);
+        }
         bool ch = false;
         for (int dg = 0; dg < ndiag; ++dg) {
-            const int ilo = max(0, dg - (my - 1) - (mz - 1));
-            const int ihi = min(mx - 1, dg);
-            const int ncand = (ihi - ilo + 1) * my;
-            for (int cnd = threadIdx.x; cnd < ncand; cnd += blockDim.x) {
-                const int ip = ilo + cnd / my, jp = cnd % my, kp = dg - ip - jp;
-                if (kp < 0 || kp >= mz) continue;
-                const int x = sx > 0 ? ip : mx - 1 - ip;
-                const int y = sy > 0 ? jp : my - 1 - jp;
-                const int z = sz > 0 ? kp : mz - 1 - kp;
-                const int idx = (z * my + y) * mx + x;
-                T vm[3], vp[3];
-                vm[0] = x > 0 ? su[idx - 1] : INF;
-                vp[0] = x + 1 < mx ? su[idx + 1] : INF;
-                vm[1] = y > 0 ? su[idx - mx] : INF;
-                vp[1] = y + 1 < my ? su[idx + mx] : INF;
-                vm[2] = z > 0 ? su[idx - mx * my] : INF;
-                vp[2] = z + 1 < mz ? su[idx + mx * my] : INF;
-                const T self = su[idx];
-                bool c1 = false;
-                const T nw = pol.update(self, vm, vp, x, y, z, idx, c1);
-                if (c1) {
-                    su[idx] = nw;
+#pragma unroll
+            for (int t = 0; t < BOX3_COLS; ++t) {
+                const int kp = dg + 1 - base[t];
+                if (kp >= 0 && kp < mz) nxt[t] = pol.load(cx[t], cy[t], zof(kp), (zof(kp) * my + cy[t]) * mx + cx[t]);
+            }
+            // gather every owned node of this hyperplane, then compute, then
+            // store (nodes of one hyperplane never read each other)
+            T vmv[BOX3_COLS][3], vpv[BOX3_COLS][3], sf[BOX3_COLS], nw[BOX3_COLS];
+            int qi[BOX3_COLS];
+            bool on[BOX3_COLS], c1[BOX3_COLS];
+#pragma unroll
+            for (int t = 0; t < BOX3_COLS; ++t) {
+                const int kp = dg - base[t];
+                on[t] = kp >= 0 && kp < mz;
+                c1[t] = false;
+                if (on[t]) {
+                    const int x = cx[t], y = cy[t], z = zof(kp);
+                    const int idx = z * plane + y * mx + x;
+                    qi[t] = idx;
+                    vmv[t][0] = x > 0 ? su[idx - 1] : INF;
+                    vpv[t][0] = x + 1 < mx ? su[idx + 1] : INF;
+                    vmv[t][1] = y > 0 ? su[idx - mx] : INF;
+                    vpv[t][1] = y + 1 < my ? su[idx + mx] : INF;
+                    vmv[t][2] = z > 0 ? su[idx - plane] : INF;
+                    vpv[t][2] = z + 1 < mz ? su[idx + plane] : INF;
+                    sf[t] = su[idx];
+                    pol.fill(cur[t], idx);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < BOX3_COLS; ++t)
+                if (on[t]) nw[t] = pol.apply(sf[t], vmv[t], vpv[t], cur[t], qi[t], c1[t]);
+#pragma unroll
+            for (int t = 0; t < BOX3_COLS; ++t)
+                if (on[t] && c1[t]) {
+                    su[qi[t]] = nw[t];
                     ch = true;
+                }
+            // columns beyond the prefetched ones (wide boxes)
+            for (int c = threadIdx.x + BOX3_COLS * blockDim.x; c < ncol; c += blockDim.x) {
+                const int x = c % mx, y = c / mx;
+                const int kp = dg - ((sx > 0 ? x : mx - 1 - x) + (sy > 0 ? y : my - 1 - y));
+                if (kp >= 0 && kp < mz) {
+                    const int z = zof(kp);
+                    node(x, y, z, pol.load(x, y, z, (z * my + y) * mx + x), ch);
                 }
             }
             __syncthreads();
+#pragma unroll
+            for (int t = 0; t < BOX3_COLS; ++t) cur[t] = nxt[t];
         }
         ++sweeps;
         if (!__syncthreads_or(ch ? 1 : 0)) {
@@ -139,12 +221,20 @@ struct Fsm3 {
     const T *r;            // per box node, via rix
     long long r0, rsx, rsy, rsz;  // global index of box node (x,y,z) = r0 + x*rsx + y*rsy + z*rsz
     T hs;
-    __device__ __forceinline__ T update(T self, const T *vm, const T *vp, int x, int y, int z, int idx,
-                                        bool &changed) const {
-        if (fixed[idx]) return self;
-        const T rv = r[r0 + x * rsx + y * rsy + z * rsz];
+    struct Stat {
+        T r;
+        uint8_t fixed;
+    };
+    __device__ __forceinline__ Stat load(int x, int y, int z, int) const {
+        return Stat{r[r0 + x * rsx + y * rsy + z * rsz], 0};
+    }
+    // shared-memory part of the node's data, read when the node is gathered
+    __device__ __forceinline__ void fill(Stat &st, int idx) const { st.fixed = fixed[idx]; }
+    __device__ __forceinline__ T apply(T self, const T *vm, const T *vp, const Stat &st, int,
+                                       bool &changed) const {
+        if (st.fixed) return self;
         uint8_t w;
-        const T ut = local_solve3(vm, vp, Num<T>::mul(rv, hs), w);
+        const T ut = local_solve3(vm, vp, Num<T>::mul(st.r, hs), w);
         changed = ut < self;
         return changed ? ut : self;
     }
@@ -157,15 +247,23 @@ struct Alg5_3 {
     const uint8_t *mask;
     long long off;
     T Hs, theta;
-    __device__ __forceinline__ T update(T self, const T *vm, const T *vp, int, int, int, int idx,
-                                        bool &changed) const {
-        using N = Num<T>;
+    struct Stat {
+        T rc, uk, cold;
+        uint8_t m;
+    };
+    __device__ __forceinline__ Stat load(int, int, int, int idx) const {
         const long long a = off + idx;
-        const uint8_t m = mask[a];
+        return Stat{rc[a], uk[a], cold[a], mask[a]};
+    }
+    __device__ __forceinline__ void fill(Stat &, int) const {}
+    __device__ __forceinline__ T apply(T self, const T *vm, const T *vp, const Stat &st, int,
+                                       bool &changed) const {
+        using N = Num<T>;
+        const uint8_t m = st.m;
         if (m & 1) return self;
         uint8_t w;
-        const T Ut = local_solve3(vm, vp, N::mul(rc[a], Hs), w);
-        const T ukv = uk[a], cv = cold[a];
+        const T Ut = local_solve3(vm, vp, N::mul(st.rc, Hs), w);
+        const T ukv = st.uk, cv = st.cold;
         bool pass = (Ut < N::inf()) && (cv < N::inf());
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
@@ -218,14 +316,16 @@ __device__ void grid3_winds(const DD3Args<T> &A, const Grid3 &d, const T *su, T 
         const long long a = d.off + e;
         uint8_t w = WIND_ZERO;
         const T rv = A.rc[a];
-        if (rv > T(0) && su[e] < INF) {
+        const int ps = box3_ps(d.mx, d.my);
+        const int q = z * ps + y * d.mx + x;
+        if (rv > T(0) && su[q] < INF) {
             T vm[3], vp[3];
-            vm[0] = x > 0 ? su[e - 1] : INF;
-            vp[0] = x + 1 < d.mx ? su[e + 1] : INF;
-            vm[1] = y > 0 ? su[e - d.mx] : INF;
-            vp[1] = y + 1 < d.my ? su[e + d.mx] : INF;
-            vm[2] = z > 0 ? su[e - d.mx * d.my] : INF;
-            vp[2] = z + 1 < d.mz ? su[e + d.mx * d.my] : INF;
+            vm[0] = x > 0 ? su[q - 1] : INF;
+            vp[0] = x + 1 < d.mx ? su[q + 1] : INF;
+            vm[1] = y > 0 ? su[q - d.mx] : INF;
+            vp[1] = y + 1 < d.my ? su[q + d.mx] : INF;
+            vm[2] = z > 0 ? su[q - ps] : INF;
+            vp[2] = z + 1 < d.mz ? su[q + ps] : INF;
             (void)local_solve3(vm, vp, Num<T>::mul(rv, Hs), w);
         }
         A.W[a] = w;
@@ -234,22 +334,24 @@ __device__ void grid3_winds(const DD3Args<T> &A, const Grid3 &d, const T *su, T 
 
 // Step 1: FSM with Alg. 1 on every shifted grid (one CTA per grid).
 template <class T>
-__global__ void k3_step1(DD3Args<T> A) {
+__global__ void __launch_bounds__(BOX3_THREADS, 1) k3_step1(DD3Args<T> A) {
     extern __shared__ __align__(16) char smem[];
     const Grid3 d = A.grids[blockIdx.x];
     const int n = d.mx * d.my * d.mz;
+    const int ps = box3_ps(d.mx, d.my);
     T *su = reinterpret_cast<T *>(smem);
-    uint8_t *fx = reinterpret_cast<uint8_t *>(su + n);
+    uint8_t *fx = reinterpret_cast<uint8_t *>(su + (size_t)d.mz * ps);
+    auto sq = [&](int e) { return (e / (d.mx * d.my)) * ps + e % (d.mx * d.my); };
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        su[e] = A.U0[d.off + e];
-        fx[e] = A.rc[d.off + e] > T(0) ? 0 : 1;
+        su[sq(e)] = A.U0[d.off + e];
+        fx[sq(e)] = A.rc[d.off + e] > T(0) ? 0 : 1;
     }
     __syncthreads();
     Fsm3<T> pol{fx, A.rc, d.off, 1, d.mx, (long long)d.mx * d.my, T(A.G.H)};
     long long sweeps;
     bool conv;
     box3_sweeps(su, d.mx, d.my, d.mz, pol, A.max_coarse, sweeps, conv);
-    for (int e = threadIdx.x; e < n; e += blockDim.x) A.U[d.off + e] = su[e];
+    for (int e = threadIdx.x; e < n; e += blockDim.x) A.U[d.off + e] = su[sq(e)];
     grid3_winds(A, d, su, T(A.G.H));
     if (threadIdx.x == 0) {
         atomicMax(&A.st->coarse_sweeps_max, (unsigned long long)sweeps);
@@ -260,34 +362,37 @@ __global__ void k3_step1(DD3Args<T> A) {
 
 // Step 4: Alg. 5 on every shifted grid.
 template <class T>
-__global__ void k3_step4(DD3Args<T> A) {
+__global__ void __launch_bounds__(BOX3_THREADS, 1) k3_step4(DD3Args<T> A) {
     if (*A.done) return;
     extern __shared__ __align__(16) char smem[];
     const Grid3 d = A.grids[blockIdx.x];
     const int n = d.mx * d.my * d.mz;
     const T INF = Num<T>::inf();
     const T Hs = T(A.G.H);
+    const int ps = box3_ps(d.mx, d.my);
     T *su = reinterpret_cast<T *>(smem);
-    for (int e = threadIdx.x; e < n; e += blockDim.x) su[e] = A.U[d.off + e];
+    auto sq = [&](int e) { return (e / (d.mx * d.my)) * ps + e % (d.mx * d.my); };
+    for (int e = threadIdx.x; e < n; e += blockDim.x) su[sq(e)] = A.U[d.off + e];
     __syncthreads();
     // C_H(nbrs^H(U^k)) and U^k for the delta
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int x = e % d.mx, y = (e / d.mx) % d.my, z = e / (d.mx * d.my);
+        const int q = sq(e);
         const long long a = d.off + e;
-        A.Uprev[a] = su[e];
+        A.Uprev[a] = su[q];
         T vm[3], vp[3];
-        vm[0] = x > 0 ? su[e - 1] : INF;
-        vp[0] = x + 1 < d.mx ? su[e + 1] : INF;
-        vm[1] = y > 0 ? su[e - d.mx] : INF;
-        vp[1] = y + 1 < d.my ? su[e + d.mx] : INF;
-        vm[2] = z > 0 ? su[e - d.mx * d.my] : INF;
-        vp[2] = z + 1 < d.mz ? su[e + d.mx * d.my] : INF;
+        vm[0] = x > 0 ? su[q - 1] : INF;
+        vp[0] = x + 1 < d.mx ? su[q + 1] : INF;
+        vm[1] = y > 0 ? su[q - d.mx] : INF;
+        vp[1] = y + 1 < d.my ? su[q + d.mx] : INF;
+        vm[2] = z > 0 ? su[q - ps] : INF;
+        vp[2] = z + 1 < d.mz ? su[q + ps] : INF;
         const T rv = A.rc[a];
         uint8_t w;
         A.cold[a] = local_solve3(vm, vp, Num<T>::mul(rv > T(0) ? rv : T(0), Hs), w);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < n; e += blockDim.x) su[e] = A.U0[d.off + e];  // Sec. 1.1 initialisation
+    for (int e = threadIdx.x; e < n; e += blockDim.x) su[sq(e)] = A.U0[d.off + e];  // Sec. 1.1 initialisation
     __threadfence_block();
     __syncthreads();
     Alg5_3<T> pol{A.rc, A.uk, A.cold, A.mask, d.off, Hs, A.theta};
@@ -295,7 +400,7 @@ __global__ void k3_step4(DD3Args<T> A) {
     bool conv;
     box3_sweeps(su, d.mx, d.my, d.mz, pol, A.max_coarse, sweeps, conv);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        A.U[d.off + e] = su[e];
+        A.U[d.off + e] = su[sq(e)];
         A.W[d.off + e] = A.wk[d.off + e];  // W = w^k
     }
     if (threadIdx.x == 0) {
@@ -324,7 +429,7 @@ __device__ __forceinline__ bool tile3_inflow(const DD3Args<T> &A, const int *l, 
 }
 
 template <class T>
-__global__ void k3_fine(DD3Args<T> A) {
+__global__ void __launch_bounds__(BOX3_THREADS, 1) k3_fine(DD3Args<T> A) {
     if (*A.done) return;
     extern __shared__ __align__(16) char smem[];
     const DD3Geom &G = A.G;
@@ -333,8 +438,9 @@ __global__ void k3_fine(DD3Args<T> A) {
     const int mx = G.S[0] + 1, my = G.S[1] + 1, mz = G.S[2] + 1;
     const int n = mx * my * mz;
     const T INF = Num<T>::inf();
+    const int ps = box3_ps(mx, my);
     T *su = reinterpret_cast<T *>(smem);
-    uint8_t *fx = reinterpret_cast<uint8_t *>(su + n);
+    uint8_t *fx = reinterpret_cast<uint8_t *>(su + (size_t)mz * ps);
     const int b0 = t0 * G.S[0], b1 = t1 * G.S[1], b2 = t2 * G.S[2];
     // Step 2: boundary data; interior and outflow nodes start at +inf
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
@@ -351,8 +457,9 @@ __global__ void k3_fine(DD3Args<T> A) {
             v = A.U[ca];
             fixed = 2;
         }
-        su[e] = v;
-        fx[e] = fixed;
+        const int q = l[2] * ps + l[1] * mx + l[0];
+        su[q] = v;
+        fx[q] = fixed;
     }
     __syncthreads();
     Fsm3<T> pol{fx, A.r, (long long)fidx(A, b0, b1, b2), 1, A.sy, A.sz, T(G.h)};
@@ -369,23 +476,24 @@ __global__ void k3_fine(DD3Args<T> A) {
         const int l[3] = {e % mx, (e / mx) % my, e / (mx * my)};
         const int Xg[3] = {b0 + l[0], b1 + l[1], b2 + l[2]};
         const size_t f = fidx(A, Xg[0], Xg[1], Xg[2]);
-        const T uv = su[e];
+        const int q = l[2] * ps + l[1] * mx + l[0];
+        const T uv = su[q];
         if (!coarse_axes3(Xg[0], Xg[1], Xg[2], G.c)) {
             A.u_out[f] = uv;
             continue;
         }
         const long long ca = coarse_addr3(A, Xg[0], Xg[1], Xg[2]);
         uint8_t w = WIND_ZERO;
-        if (fx[e] == 2) {
+        if (fx[q] == 2) {
             w = A.W[ca];
-        } else if (fx[e] == 0 && uv < INF) {
+        } else if (fx[q] == 0 && uv < INF) {
             T vm[3], vp[3];
-            vm[0] = l[0] > 0 ? su[e - 1] : INF;
-            vp[0] = l[0] + 1 < mx ? su[e + 1] : INF;
-            vm[1] = l[1] > 0 ? su[e - mx] : INF;
-            vp[1] = l[1] + 1 < my ? su[e + mx] : INF;
-            vm[2] = l[2] > 0 ? su[e - mx * my] : INF;
-            vp[2] = l[2] + 1 < mz ? su[e + mx * my] : INF;
+            vm[0] = l[0] > 0 ? su[q - 1] : INF;
+            vp[0] = l[0] + 1 < mx ? su[q + 1] : INF;
+            vm[1] = l[1] > 0 ? su[q - mx] : INF;
+            vp[1] = l[1] + 1 < my ? su[q + mx] : INF;
+            vm[2] = l[2] > 0 ? su[q - ps] : INF;
+            vp[2] = l[2] + 1 < mz ? su[q + ps] : INF;
             (void)local_solve3(vm, vp, Num<T>::mul(A.r[f], T(G.h)), w);
         }
         int slot = 0;
@@ -644,13 +752,13 @@ static bool dd3_plan(const eik_grid *grid, const eik_dd_params *p, DD3Plan &P) {
     G.ng = (int)P.grids.size();
     G.nc = off;
     const size_t tsz = grid->dtype == EIK_F64 ? 8 : 4;
-    const size_t tile_n = (size_t)(G.S[0] + 1) * (G.S[1] + 1) * (G.S[2] + 1);
+    const size_t tile_n = (size_t)(G.S[2] + 1) * box3_ps(G.S[0] + 1, G.S[1] + 1);
     size_t gmax = 0;
-    for (auto &d : P.grids) gmax = std::max(gmax, (size_t)d.mx * d.my * d.mz);
+    for (auto &d : P.grids) gmax = std::max(gmax, (size_t)d.mz * box3_ps(d.mx, d.my));
     P.fine_smem = tile_n * (tsz + 1) + 16;
     P.grid_smem = gmax * (tsz + 1) + 16;
-    P.fine_threads = 512;
-    P.grid_threads = 512;
+    P.fine_threads = BOX3_THREADS;
+    P.grid_threads = BOX3_THREADS;
     return true;
 }
 
