@@ -189,11 +189,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="dd4097", choices=["dd4097", "batch256", "dd3d257", "tomography1025"],
+                    help="dd4097 (default) is the benchmark line; the others measure the batched solve, the "
+                         "3-D solve and the tomography gradient with the same keys")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "dd4097":
+        return run_extra(args)
 
     import torch
     from paper_1805_04198_gb300 import eik
@@ -385,6 +390,212 @@ def main():
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+# --------------------------------------------------------------------------
+# Further workloads (not the benchmark line): same keys, own metric.
+# --------------------------------------------------------------------------
+def _timed(torch, fn, steps, warmup, flush, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        fn()
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / steps
+
+
+def _profiled(torch, eik, fn):
+    eik.eik_profile_enable(True)
+    fn()
+    torch.cuda.synchronize()
+    eik.eik_profile_enable(False)
+    return eik.eik_profile_collect()
+
+
+def run_extra(args):
+    import torch
+    from paper_1805_04198_gb300 import eik
+    import oracle
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    eik.load()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peak, peak_kind = load_peaks()
+    cpu = None
+    extra = {}
+    t = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a)).to(dev) if dt is None else \
+        torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+
+    if args.workload == "batch256":
+        w = inputs.workload_c3()
+        probs = [dict(r=t(q["r"].astype(np.float32)), gamma=t(q["gamma"]), g=t(q["g"].astype(np.float32)),
+                      h=q["h"], tiles=q["tiles"], coarse_ratio=q["c"], theta=q["theta"], max_iter=q["max_iter"],
+                      tol=q["tol"]) for q in w]
+        B = eik.DDBatch(probs)
+        best, tune_ms = B.autotune(tune_iters=2)
+        prof = _profiled(torch, eik, B.run)
+        B.capture()
+        with ClockSampler(local_rank) as clk:
+            ms = _timed(torch, B.replay, args.steps, args.warmup, flush, stream)
+        st = B.stats()
+        upd = sum(x["fine_updates"] + x["coarse_updates"] for x in st)
+        fine_upd = sum(x["fine_updates"] for x in st)
+        fine_ms = prof["dd_fine_subdomains"]["total_ms"]
+        kern = ("dd_fine_subdomains", fine_upd * BYTES_PER_UPDATE_F32 / (fine_ms / 1e3) / 1e9)
+        extra = {"autotuned": {"fine_queue": best.fine_queue, "coarse_queue": best.coarse_queue,
+                               "ctas_per_sm": best.ctas_per_sm, "largest_first": best.largest_first,
+                               "tune_ms": tune_ms},
+                 "launches_per_solve": st[0]["launches"], "graph": True,
+                 "iters": sorted(set(x["iters"] for x in st))}
+        # end to end: pinned host inputs in, every u out, each step
+        hr = [torch.from_numpy(q["r"].astype(np.float32)).pin_memory() for q in w]
+        hu = [torch.empty_like(x).pin_memory() for x in hr]
+        def e2e_step():
+            for p, x in zip(probs, hr):
+                p["r"].copy_(x, non_blocking=True)
+            B.replay()
+            for y, u in zip(hu, B.u):
+                y.copy_(u, non_blocking=True)
+        e2e_ms = _timed(torch, e2e_step, max(1, args.steps // 2), 1, flush, stream)
+        h2d = sum(x.numel() * 4 for x in hr)
+        e2e = {"value": upd / (e2e_ms / 1e3) / 1e9, "unit": "Gupdates/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": h2d, "ms_per_step": e2e_ms,
+               "note": "slowness of every problem in, every u out (sources stay resident)"}
+        workload = {"workload": "batch_256_mixed_2d", "nprob": len(w), "sides": [257, 513, 1025, 2049],
+                    "tiles": [8, 16, 32], "theta": 0.2, "cap": "2T+10",
+                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
+        unit, metric = "Gupdates/s", "batched DD: local solves per second over a 256-problem mixed batch"
+        if rank == 0 and not args.no_cpu_baseline:
+            small = [i for i, q in enumerate(w) if q["r"].shape[0] == 257][:2]
+            t0 = time.perf_counter()
+            cu = 0
+            for i in small:
+                q = w[i]
+                _, so, _ = oracle.dd(q["r"].astype(np.float32).astype(np.float64), q["gamma"], q["g"], q["h"],
+                                     q["tiles"], q["c"], theta=q["theta"], max_iter=q["max_iter"], tol=q["tol"],
+                                     max_coarse_sweeps=8)
+                cu += so["fine_updates"] + so["coarse_updates"]
+            dt = time.perf_counter() - t0
+            cpu = {"value": cu / dt / 1e9, "unit": unit, "cores": 1, "kind": "oracle",
+                   "sample": "the first two 257^2 problems of the batch, full solves, %.1f s" % dt}
+        value = upd * world / (ms / 1e3) / 1e9
+    elif args.workload == "dd3d257":
+        w = inputs.workload_c2()
+        R, G, g = t(w["r"].astype(np.float32)), t(w["gamma"]), t(w["g"].astype(np.float32))
+        kw = dict(theta=0.2, max_iter=w["max_iter"], tol=0.0, max_coarse_sweeps=8)
+        grid = eik.make_grid(R, w["h"])
+        params = eik.dd_params(w["tiles"], w["c"], **kw)
+        ws = torch.empty(eik.eik_dd_workspace_size(grid, params) + 256, dtype=torch.uint8, device=dev)
+        u = torch.empty_like(R)
+        st_dev = torch.zeros(eik.ctypes.sizeof(eik.DDStats), dtype=torch.uint8, device=dev)
+        solve = lambda: eik.eik_dd_solve(grid, R, G, g, params, u, ws, st_dev, stream)
+        prof = _profiled(torch, eik, solve)
+        with ClockSampler(local_rank) as clk:
+            ms = _timed(torch, solve, args.steps, args.warmup, flush, stream)
+        st = eik.parse_dd_stats(st_dev)
+        upd = st["fine_updates"] + st["coarse_updates"]
+        fine_ms = prof["dd3_fine_subdomains"]["total_ms"]
+        kern = ("dd3_fine_subdomains", st["fine_updates"] * BYTES_PER_UPDATE_F32 / (fine_ms / 1e3) / 1e9)
+        extra = {"dd_stats": {k: st[k] for k in ("iters", "fsm_sweeps_max", "fine_updates", "coarse_updates")},
+                 "kernel_ms": {k: v["total_ms"] for k, v in prof.items()}}
+        hr = torch.from_numpy(w["r"].astype(np.float32)).pin_memory()
+        hu = torch.empty_like(hr).pin_memory()
+        def e2e_step():
+            R.copy_(hr, non_blocking=True)
+            solve()
+            hu.copy_(u, non_blocking=True)
+        e2e_ms = _timed(torch, e2e_step, max(1, args.steps // 2), 1, flush, stream)
+        e2e = {"value": upd / (e2e_ms / 1e3) / 1e9, "unit": "Gupdates/s", "h2d_bytes_per_step": hr.numel() * 4,
+               "d2h_bytes_per_step": hu.numel() * 4, "ms_per_step": e2e_ms}
+        workload = {"workload": "dd3d_257_pointsrc_8x8x8_c8", "n": 257, "tiles": 8, "coarse_ratio": 8, **kw,
+                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
+        unit, metric = "Gupdates/s", "3-D DD: local solves per second, 257^3"
+        if rank == 0 and not args.no_cpu_baseline:
+            t0 = time.perf_counter()
+            _, so, _ = oracle.dd(w["r"].astype(np.float32).astype(np.float64), w["gamma"], w["g"], w["h"],
+                                 w["tiles"], w["c"], theta=0.2, max_iter=0, tol=0.0, max_coarse_sweeps=8)
+            dt = time.perf_counter() - t0
+            cu = so["fine_updates"] + so["coarse_updates"]
+            cpu = {"value": cu / dt / 1e9, "unit": unit, "cores": 1, "kind": "oracle",
+                   "sample": "Step 1 + one fine pass over all 512 subdomains (max_iter=0), %.1f s" % dt}
+        value = upd * world / (ms / 1e3) / 1e9
+    else:
+        w = inputs.workload_c4()
+        n, h = w["n"], w["h"]
+        R = t(w["r0"].astype(np.float32))
+        g0 = torch.zeros_like(R)
+        rec = torch.tensor([j * n + n - 1 for j in w["rec_rows"]], device=dev)
+        gams, data = [], []
+        for srow in w["src_rows"]:
+            gm = torch.zeros((n, n), dtype=torch.uint8, device=dev)
+            gm[srow, 0] = 1
+            gams.append(gm)
+            ut, _ = eik.fsm(t(w["r_true"].astype(np.float32)), gm, g0, h)
+            data.append(ut.flatten()[rec].clone())
+        def gradient():
+            rr = R.detach().requires_grad_(True)
+            L = 0.0
+            for gm, d in zip(gams, data):
+                u = eik.EikonalSolve.apply(rr, gm, g0, h)
+                L = L + 0.5 * ((u.flatten()[rec] - d) ** 2).sum()
+            L.backward()
+            return rr.grad
+        prof = _profiled(torch, eik, gradient)
+        with ClockSampler(local_rank) as clk:
+            ms = _timed(torch, gradient, args.steps, args.warmup, flush, stream)
+        fs = prof.get("fsm_sweeps", {"total_ms": float("nan")})
+        extra = {"kernel_ms": {k: v["total_ms"] for k, v in prof.items()}, "sources": len(gams),
+                 "receivers": len(w["rec_rows"])}
+        # per-source sweeps for the algorithmic byte count of the forward kernel
+        _, fst = eik.fsm(R, gams[0], g0, h)
+        fwd_upd = fst["updates"] * len(gams)
+        kern = ("fsm_sweeps", fwd_upd * BYTES_PER_UPDATE_F32 / (fs["total_ms"] / 1e3) / 1e9)
+        hr = torch.from_numpy(w["r0"].astype(np.float32)).pin_memory()
+        hg = torch.empty_like(hr).pin_memory()
+        def e2e_step():
+            R.copy_(hr, non_blocking=True)
+            gr = gradient()
+            hg.copy_(gr, non_blocking=True)
+        e2e_ms = _timed(torch, e2e_step, max(1, args.steps // 2), 1, flush, stream)
+        e2e = {"value": len(gams) / (e2e_ms / 1e3), "unit": "sources/s", "h2d_bytes_per_step": hr.numel() * 4,
+               "d2h_bytes_per_step": hg.numel() * 4, "ms_per_step": e2e_ms}
+        workload = {"workload": "tomography_1025_64src_256rec", "n": n, "sources": 64, "receivers": 256,
+                    "forward": "fsm", "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
+        unit, metric = "sources/s", "travel-time tomography: gradient dL/dr, sources (forward + adjoint) per second"
+        if rank == 0 and not args.no_cpu_baseline:
+            t0 = time.perf_counter()
+            gam = np.zeros((n, n), np.uint8)
+            gam[w["src_rows"][0], 0] = 1
+            r64 = w["r0"].astype(np.float32).astype(np.float64)
+            u0, _, _ = oracle.fsm(r64, gam, 0.0, h)
+            dJ = np.zeros((n, n))
+            dJ[w["rec_rows"], n - 1] = 1.0
+            oracle.adjoint(r64, gam, u0, dJ, h)
+            dt = time.perf_counter() - t0
+            cpu = {"value": 1.0 / dt, "unit": unit, "cores": 1, "kind": "oracle",
+                   "sample": "one source: forward FSM + adjoint, FP64, %.1f s" % dt}
+        value = len(gams) * world / (ms / 1e3)
+    if rank == 0:
+        line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload,
+                "roofline": {"bound": "hbm", "achieved": kern[1], "peak": peak, "unit": "GB/s",
+                             "frac": kern[1] / peak, "traffic": None, "kernel": kern[0], "peak_source": peak_kind,
+                             "algorithmic_bytes": "12 B per node update (u in, r in, u out)"},
+                "gpu_launches": sum(v["launches"] for v in prof.values()) * args.steps, "e2e": e2e,
+                "clocks": clk.summary(), "cpu_baseline": cpu, **extra}
+        print(json.dumps(line))
     return 0
 
 
