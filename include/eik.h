@@ -87,6 +87,25 @@ size_t eik_fsm_workspace_size(const eik_grid *grid);
 int eik_fsm(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, void *u,
             int64_t max_sweeps, void *ws, size_t ws_bytes, eik_fsm_stats *stats, void *stream);
 
+/* Workspace for eik_fsm_many; 0 if invalid. */
+size_t eik_fsm_many_workspace_size(const eik_grid *grid, int nprob);
+
+/*
+ * eik_fsm_many: nprob problems on one grid and one slowness r, differing in
+ * their sources: problem p is eik_fsm(grid, r, gamma[p], g[p], u[p], ...).
+ * Each problem's result and statistics are exactly those of its own eik_fsm
+ * call; the problems run concurrently (one launch per stage for all of them).
+ * A project addition for many-source workloads such as travel-time
+ * tomography; the paper solves one source set at a time.
+ *   nprob        1 .. 65535
+ *   gamma, g, u  host arrays [nprob] of device pointers, each laid out as grid
+ *   ws           scratch of eik_fsm_many_workspace_size() bytes, 256-byte aligned
+ *   stats        device array [nprob] (may be NULL)
+ */
+int eik_fsm_many(const eik_grid *grid, int nprob, const void *r, const uint8_t *const *gamma,
+                 const void *const *g, void *const *u, int64_t max_sweeps, void *ws, size_t ws_bytes,
+                 eik_fsm_stats *stats, void *stream);
+
 /* ------------------------------------------------------------------------- */
 /* Two-scale domain decomposition (Sec. 3.2, Steps 1-4, Alg. 1-5).            */
 /* ------------------------------------------------------------------------- */
@@ -174,6 +193,25 @@ size_t eik_dd_adjoint_workspace_size(const eik_grid *grid);
 int eik_dd_adjoint(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *u, const void *dJdu,
                    void *grad_r, int64_t max_sweeps, void *ws, size_t ws_bytes, eik_adjoint_stats *stats,
                    void *stream);
+
+/* Workspace for eik_dd_adjoint_many; 0 if invalid. */
+size_t eik_dd_adjoint_many_workspace_size(const eik_grid *grid, int nprob);
+
+/*
+ * eik_dd_adjoint_many: the adjoint of eik_dd_adjoint for nprob problems on
+ * one grid and one slowness r (problem p: sources gamma[p], forward solution
+ * u[p], dJ/du of that problem dJdu[p]).  grad_r[p] (when grad_r and grad_r[p]
+ * are not NULL) receives exactly eik_dd_adjoint's result for problem p;
+ * grad_sum (when not NULL) receives g_0 + g_1 + ... + g_{nprob-1} of those
+ * gradients, added in problem order.  At least one of grad_r and grad_sum is
+ * given.  A project addition (gradient of a sum of per-source misfits).
+ *   gamma, u, dJdu, grad_r   host arrays [nprob] of device pointers
+ *   ws     scratch of eik_dd_adjoint_many_workspace_size() bytes, 256-byte aligned
+ *   stats  device array [nprob] (may be NULL)
+ */
+int eik_dd_adjoint_many(const eik_grid *grid, int nprob, const void *r, const uint8_t *const *gamma,
+                        const void *const *u, const void *const *dJdu, void *const *grad_r, void *grad_sum,
+                        int64_t max_sweeps, void *ws, size_t ws_bytes, eik_adjoint_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* Batched DD: many independent 2-D problems of mixed sizes, each solved by    */

@@ -20,6 +20,9 @@
 #include "engine.cuh"
 #include "host_util.h"
 #include "prof.h"
+#include "ptr_table.cuh"
+
+#include <vector>
 
 namespace eik {
 
@@ -89,18 +92,22 @@ __device__ void adj_node(const AdjArgs<T> &A, int x, int y, T wm[2], T wp[2], T 
 }
 
 template <class T>
-__global__ void k_adj_zero(AdjArgs<T> A) {
+__device__ void adj_zero_body(const AdjArgs<T> &A, size_t bid, size_t nbid) {
     const size_t n = (size_t)A.nx * A.ny;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < 4 * n; t += (size_t)gridDim.x * blockDim.x)
-        A.win[t] = T(0);
+    for (size_t t = bid * blockDim.x + threadIdx.x; t < 4 * n; t += nbid * blockDim.x) A.win[t] = T(0);
+}
+
+template <class T>
+__global__ void k_adj_zero(AdjArgs<T> A) {
+    adj_zero_body(A, blockIdx.x, gridDim.x);
 }
 
 // each node scatters the weights of its dependencies into its neighbours'
 // incoming slots (every slot has exactly one writer)
 template <class T>
-__global__ void k_adj_nodes(AdjArgs<T> A) {
+__device__ void adj_nodes_body(const AdjArgs<T> &A, size_t bid, size_t nbid) {
     const size_t n = (size_t)A.nx * A.ny;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    for (size_t t = bid * blockDim.x + threadIdx.x; t < n; t += nbid * blockDim.x) {
         const int x = (int)(t % A.nx), y = (int)(t / A.nx);
         T wm[2], wp[2], dr;
         adj_node(A, x, y, wm, wp, dr);
@@ -114,10 +121,15 @@ __global__ void k_adj_nodes(AdjArgs<T> A) {
 }
 
 template <class T>
-__global__ void k_adj_pack(AdjArgs<T> A) {
+__global__ void k_adj_nodes(AdjArgs<T> A) {
+    adj_nodes_body(A, blockIdx.x, gridDim.x);
+}
+
+template <class T>
+__device__ void adj_pack_body(const AdjArgs<T> &A, size_t bid, size_t nbid) {
     const size_t n = (size_t)A.nx * A.ny;
     const size_t chan = (size_t)4 * A.nb * A.nstepp * 32;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    for (size_t t = bid * blockDim.x + threadIdx.x; t < n; t += nbid * blockDim.x) {
         const int x = (int)(t % A.nx), y = (int)(t / A.nx);
         const T vals[5] = {A.win[t], A.win[n + t], A.win[2 * n + t], A.win[3 * n + t],
                            A.dJdu[(size_t)y * A.sy + x]};
@@ -127,6 +139,11 @@ __global__ void k_adj_pack(AdjArgs<T> A) {
         }
         A.state[box_index(x, y, A.ny)] = T(0);
     }
+}
+
+template <class T>
+__global__ void k_adj_pack(AdjArgs<T> A) {
+    adj_pack_body(A, blockIdx.x, gridDim.x);
 }
 
 // lambda_i = dJ/du_i + W(-x) l(-x) + W(+x) l(+x) + W(-y) l(-y) + W(+y) l(+y)
@@ -160,8 +177,7 @@ __device__ __forceinline__ Box<T, 5> adj_box(const AdjArgs<T> &A) {
 }
 
 template <class T>
-__global__ void k_adj_run(AdjArgs<T> A) {
-    extern __shared__ __align__(16) char smem[];
+__device__ void adj_run_body(const AdjArgs<T> &A, char *smem) {
     const Box<T, 5> bx = adj_box(A);
     AdjPolicy<T> pol;
     long long sweeps;
@@ -176,38 +192,56 @@ __global__ void k_adj_run(AdjArgs<T> A) {
 }
 
 template <class T>
+__global__ void k_adj_run(AdjArgs<T> A) {
+    extern __shared__ __align__(16) char smem[];
+    adj_run_body(A, smem);
+}
+
+template <class T>
 __global__ void k_adj_init_global(AdjArgs<T> A) {
     engine_global_init(A.gctl, A.nb);
     if (threadIdx.x == 0) A.dev->err = 0;
 }
 
 template <class T>
-__global__ void k_adj_run_global(AdjArgs<T> A) {
-    extern __shared__ __align__(16) char smem[];
+__device__ void adj_run_global_body(const AdjArgs<T> &A, char *smem, int cta) {
     const Box<T, 5> bx = adj_box(A);
     AdjPolicy<T> pol;
     long long sweeps;
     bool conv;
-    engine_run<T, 5, false, true>(bx, pol, A.max_sweeps, smem, sweeps, conv, &A.dev->err, A.ghands, A.gctl);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    engine_run<T, 5, false, true>(bx, pol, A.max_sweeps, smem, sweeps, conv, &A.dev->err, A.ghands, A.gctl, cta);
+    if (cta == 0 && threadIdx.x == 0) {
         A.dev->sweeps = (unsigned long long)sweeps;
         A.dev->converged = conv ? 1 : 0;
     }
 }
 
 template <class T>
-__global__ void k_adj_grad(AdjArgs<T> A, eik_adjoint_stats *out) {
+__global__ void k_adj_run_global(AdjArgs<T> A) {
+    extern __shared__ __align__(16) char smem[];
+    adj_run_global_body(A, smem, (int)blockIdx.x);
+}
+
+template <class T>
+__device__ void adj_grad_body(const AdjArgs<T> &A, eik_adjoint_stats *out, size_t bid, size_t nbid) {
     const size_t n = (size_t)A.nx * A.ny;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(t % A.nx), y = (int)(t / A.nx);
-        A.grad[(size_t)y * A.sy + x] = Num<T>::mul(A.state[box_index(x, y, A.ny)], A.dudr[t]);
+    if (A.grad) {
+        for (size_t t = bid * blockDim.x + threadIdx.x; t < n; t += nbid * blockDim.x) {
+            const int x = (int)(t % A.nx), y = (int)(t / A.nx);
+            A.grad[(size_t)y * A.sy + x] = Num<T>::mul(A.state[box_index(x, y, A.ny)], A.dudr[t]);
+        }
     }
-    if (out && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (out && bid == 0 && threadIdx.x == 0) {
         out->sweeps = (int64_t)A.dev->sweeps;
         out->converged = A.dev->converged;
         out->error = A.dev->err;
         out->launches = A.launches;
     }
+}
+
+template <class T>
+__global__ void k_adj_grad(AdjArgs<T> A, eik_adjoint_stats *out) {
+    adj_grad_body(A, out, blockIdx.x, gridDim.x);
 }
 
 struct AdjPlan {
@@ -320,6 +354,213 @@ static int adj_run(const eik_grid *grid, const AdjPlan &P, const void *r, const 
     return cuda_check(cudaGetLastError(), "adjoint launch");
 }
 
+
+// --------------------------------------------------------------------------
+// Many right-hand sides on one grid and one slowness (the sources of a
+// tomography problem): every per-problem kernel of adj_run covers all problems
+// in one launch (the multi-CTA sweep form in co-resident groups), and
+// optionally grad_sum = sum over problems of dJ_p/dr, added in problem order.
+// --------------------------------------------------------------------------
+template <class T>
+struct AdjMany {
+    AdjArgs<T> A;            // shared fields; the per-problem ones are set by adj_prob
+    const void *const *tab;  // [4][nprob]: gamma, u, dJdu, grad (grad entries may be null)
+    char *ws0;               // workspace of problem 0; problem p at ws0 + p * per
+    size_t per;
+    size_t o_win, o_dudr, o_state, o_sk, o_ghands, o_gctl, o_dev;
+    T *grad_sum;             // may be null
+    int nprob;
+};
+
+template <class T>
+__device__ __forceinline__ AdjArgs<T> adj_prob(const AdjMany<T> &M, int p) {
+    AdjArgs<T> A = M.A;
+    A.gamma = static_cast<const uint8_t *>(M.tab[p]);
+    A.u = static_cast<const T *>(M.tab[M.nprob + p]);
+    A.dJdu = static_cast<const T *>(M.tab[2 * M.nprob + p]);
+    A.grad = static_cast<T *>(const_cast<void *>(M.tab[3 * M.nprob + p]));
+    char *b = M.ws0 + (size_t)p * M.per;
+    A.win = reinterpret_cast<T *>(b + M.o_win);
+    A.dudr = reinterpret_cast<T *>(b + M.o_dudr);
+    A.state = reinterpret_cast<T *>(b + M.o_state);
+    A.sk = reinterpret_cast<T *>(b + M.o_sk);
+    A.ghands = reinterpret_cast<T *>(b + M.o_ghands);
+    A.gctl = reinterpret_cast<int *>(b + M.o_gctl);
+    A.dev = reinterpret_cast<AdjDev *>(b + M.o_dev);
+    return A;
+}
+
+template <class T>
+__global__ void k_adjm_zero(AdjMany<T> M) {
+    adj_zero_body(adj_prob(M, blockIdx.y), blockIdx.x, gridDim.x);
+}
+template <class T>
+__global__ void k_adjm_nodes(AdjMany<T> M) {
+    adj_nodes_body(adj_prob(M, blockIdx.y), blockIdx.x, gridDim.x);
+}
+template <class T>
+__global__ void k_adjm_pack(AdjMany<T> M) {
+    adj_pack_body(adj_prob(M, blockIdx.y), blockIdx.x, gridDim.x);
+}
+template <class T>
+__global__ void k_adjm_run(AdjMany<T> M) {
+    extern __shared__ __align__(16) char smem[];
+    adj_run_body(adj_prob(M, blockIdx.x), smem);
+}
+template <class T>
+__global__ void k_adjm_init_global(AdjMany<T> M) {
+    const AdjArgs<T> A = adj_prob(M, blockIdx.x);
+    engine_global_init(A.gctl, A.nb);
+    if (threadIdx.x == 0) A.dev->err = 0;
+}
+// CTA c of the launch serves problem p0 + c / nblk as its CTA c % nblk
+template <class T>
+__global__ void k_adjm_run_global(AdjMany<T> M, int p0, int nblk) {
+    extern __shared__ __align__(16) char smem[];
+    adj_run_global_body(adj_prob(M, p0 + (int)blockIdx.x / nblk), smem, (int)blockIdx.x % nblk);
+}
+template <class T>
+__global__ void k_adjm_grad(AdjMany<T> M, eik_adjoint_stats *out) {
+    adj_grad_body(adj_prob(M, blockIdx.y), out ? out + blockIdx.y : nullptr, blockIdx.x, gridDim.x);
+}
+// grad_sum = g_0 + g_1 + ... + g_{nprob-1}, g_p = lambda_p dF/dr of problem p,
+// accumulated left to right
+template <class T>
+__global__ void k_adjm_sum(AdjMany<T> M) {
+    const AdjArgs<T> &A = M.A;
+    const size_t n = (size_t)A.nx * A.ny;
+    const size_t per = M.per;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(t % A.nx), y = (int)(t / A.nx);
+        const size_t bi = box_index(x, y, A.ny);
+        T acc = T(0);
+        for (int p = 0; p < M.nprob; ++p) {
+            const char *b = M.ws0 + (size_t)p * per;
+            const T gp = Num<T>::mul(reinterpret_cast<const T *>(b + M.o_state)[bi],
+                                     reinterpret_cast<const T *>(b + M.o_dudr)[t]);
+            acc = p == 0 ? gp : Num<T>::add(acc, gp);
+        }
+        M.grad_sum[(size_t)y * A.sy + x] = acc;
+    }
+}
+
+struct AdjManyPlan {
+    AdjPlan P;
+    size_t tab_bytes, per, bytes;
+};
+
+static bool adj_many_plan(const eik_grid *grid, int nprob, AdjManyPlan &M) {
+    if (nprob < 1 || nprob > 65535) {
+        set_error("nprob = %d out of range [1, 65535]", nprob);
+        return false;
+    }
+    if (!adj_plan(grid, M.P)) return false;
+    M.tab_bytes = ((size_t)4 * nprob * sizeof(void *) + 255) & ~(size_t)255;
+    M.per = (M.P.bytes + 255) & ~(size_t)255;
+    M.bytes = M.tab_bytes + (size_t)nprob * M.per + 256;
+    return true;
+}
+
+template <class T>
+static int adj_many_run(const eik_grid *grid, const AdjManyPlan &MP, int nprob, const void *r,
+                        const uint8_t *const *gamma, const void *const *u, const void *const *dJdu,
+                        void *const *grad, void *grad_sum, int64_t max_sweeps, void *ws, eik_adjoint_stats *stats,
+                        cudaStream_t s) {
+    const AdjPlan &P = MP.P;
+    AdjMany<T> M;
+    memset(&M, 0, sizeof(M));
+    AdjArgs<T> &A = M.A;
+    A.r = static_cast<const T *>(r);
+    A.sy = grid->stride[1];
+    A.nx = P.nx;
+    A.ny = P.ny;
+    A.nb = P.nb;
+    A.nstepp = P.nstepp;
+    A.h = (T)grid->h;
+    A.max_sweeps = max_sweeps;
+    char *const dummy = reinterpret_cast<char *>(256);
+    AdjArgs<T> L;
+    adj_layout<T>(P, &L, dummy);
+    M.o_win = reinterpret_cast<char *>(L.win) - dummy;
+    M.o_dudr = reinterpret_cast<char *>(L.dudr) - dummy;
+    M.o_state = reinterpret_cast<char *>(L.state) - dummy;
+    M.o_sk = reinterpret_cast<char *>(L.sk) - dummy;
+    M.o_ghands = reinterpret_cast<char *>(L.ghands) - dummy;
+    M.o_gctl = reinterpret_cast<char *>(L.gctl) - dummy;
+    M.o_dev = reinterpret_cast<char *>(L.dev) - dummy;
+    M.tab = static_cast<const void *const *>(ws);
+    M.ws0 = static_cast<char *>(ws) + MP.tab_bytes;
+    M.per = MP.per;
+    M.nprob = nprob;
+    M.grad_sum = static_cast<T *>(grad_sum);
+
+    int rc, dev, optin = 0, nsm = 0;
+    if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncAttributes fa;
+    if ((rc = cuda_check(cudaFuncGetAttributes(&fa, k_adjm_run<T>), "func attr"))) return rc;
+    const bool single = (int)P.smem <= optin && P.nb <= 32 && (long long)fa.numRegs * 32 * P.nb <= 65536;
+    const int nblk = (P.nb + P.wpc - 1) / P.wpc;
+    int group = nprob;
+    if (!single) {
+        if ((rc = cuda_check(cudaFuncSetAttribute(k_adjm_run_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)P.gsmem), "smem attr")))
+            return rc;
+        int per_sm = 0;
+        if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjm_run_global<T>, 32 * P.wpc,
+                                                                          P.gsmem), "occupancy")))
+            return rc;
+        group = std::min(nprob, per_sm * nsm / nblk);
+        if (group < 1) {
+            set_error("grid of %d x %d nodes needs %d co-resident CTAs, the device holds %d", P.nx, P.ny, nblk,
+                      per_sm * nsm);
+            return EIK_EUNSUPPORTED;
+        }
+    } else if ((rc = cuda_check(cudaFuncSetAttribute(k_adjm_run<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)P.smem), "smem attr"))) {
+        return rc;
+    }
+    std::vector<const void *> tab((size_t)4 * nprob);
+    for (int p = 0; p < nprob; ++p) {
+        tab[p] = gamma[p];
+        tab[nprob + p] = u[p];
+        tab[2 * nprob + p] = dJdu[p];
+        tab[3 * nprob + p] = grad ? grad[p] : nullptr;
+    }
+    int nl = upload_ptrs(const_cast<const void **>(M.tab), tab.data(), 4 * nprob, s);
+    if (nl < 0) return nl;
+    const int ngroups = (nprob + group - 1) / group;
+    nl += 4 + (single ? 1 : 1 + ngroups) + (grad_sum ? 1 : 0);
+    A.launches = nl;
+    const size_t total = (size_t)P.nx * P.ny;
+    const dim3 eg((unsigned)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)nsm * 16 / nprob + 1)),
+                  (unsigned)nprob);
+    EIK_LAUNCH("adj_zero", s, k_adjm_zero<T><<<eg, 256, 0, s>>>(M));
+    EIK_LAUNCH("adj_nodes", s, k_adjm_nodes<T><<<eg, 256, 0, s>>>(M));
+    EIK_LAUNCH("adj_pack", s, k_adjm_pack<T><<<eg, 256, 0, s>>>(M));
+    if (single) {
+        EIK_LAUNCH("adj_sweeps", s, k_adjm_run<T><<<nprob, 32 * P.nb, P.smem, s>>>(M));
+    } else {
+        EIK_LAUNCH("adj_init", s, k_adjm_init_global<T><<<nprob, 256, 0, s>>>(M));
+        for (int p0 = 0; p0 < nprob; p0 += group) {
+            int np = std::min(group, nprob - p0);
+            void *args[] = {&M, &p0, const_cast<int *>(&nblk)};
+            int tok = prof_begin("adj_sweeps", s);
+            rc = cuda_check(cudaLaunchCooperativeKernel((void *)k_adjm_run_global<T>, np * nblk, 32 * P.wpc, args,
+                                                        P.gsmem, s),
+                            "adjoint cooperative launch");
+            prof_end(tok, s);
+            if (rc) return rc;
+        }
+    }
+    EIK_LAUNCH("adj_grad", s, k_adjm_grad<T><<<eg, 256, 0, s>>>(M, stats));
+    if (grad_sum) {
+        const int sb = (int)std::min<size_t>((total + 255) / 256, (size_t)nsm * 16);
+        EIK_LAUNCH("adj_sum", s, k_adjm_sum<T><<<sb, 256, 0, s>>>(M));
+    }
+    return cuda_check(cudaGetLastError(), "adjoint launch");
+}
 }  // namespace eik
 
 using namespace eik;
@@ -354,4 +595,44 @@ extern "C" int eik_dd_adjoint(const eik_grid *grid, const void *r, const uint8_t
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (grid->dtype == EIK_F64) return adj_run<double>(grid, P, r, gamma, u, dJdu, grad_r, max_sweeps, ws, stats, s);
     return adj_run<float>(grid, P, r, gamma, u, dJdu, grad_r, max_sweeps, ws, stats, s);
+}
+
+extern "C" size_t eik_dd_adjoint_many_workspace_size(const eik_grid *grid, int nprob) {
+    AdjManyPlan M;
+    if (!adj_many_plan(grid, nprob, M)) return 0;
+    return M.bytes;
+}
+
+extern "C" int eik_dd_adjoint_many(const eik_grid *grid, int nprob, const void *r, const uint8_t *const *gamma,
+                                   const void *const *u, const void *const *dJdu, void *const *grad_r,
+                                   void *grad_sum, int64_t max_sweeps, void *ws, size_t ws_bytes,
+                                   eik_adjoint_stats *stats, void *stream) {
+    AdjManyPlan M;
+    if (!adj_many_plan(grid, nprob, M)) return EIK_EINVAL;
+    if (!r || !gamma || !u || !dJdu || !ws || (!grad_r && !grad_sum)) {
+        set_error("eik_dd_adjoint_many: NULL argument (grad_r and grad_sum may not both be NULL)");
+        return EIK_EINVAL;
+    }
+    for (int p = 0; p < nprob; ++p) {
+        if (!gamma[p] || !u[p] || !dJdu[p]) {
+            set_error("eik_dd_adjoint_many: NULL array of problem %d", p);
+            return EIK_EINVAL;
+        }
+    }
+    if (max_sweeps < 1 || max_sweeps > MAX_SWEEPS) {
+        set_error("max_sweeps must be in [1, %lld]", MAX_SWEEPS);
+        return EIK_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) & 255) {
+        set_error("workspace must be 256-byte aligned");
+        return EIK_EINVAL;
+    }
+    if (ws_bytes < M.bytes) {
+        set_error("workspace of %zu bytes is smaller than the %zu required", ws_bytes, M.bytes);
+        return EIK_ENOMEM;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grid->dtype == EIK_F64)
+        return adj_many_run<double>(grid, M, nprob, r, gamma, u, dJdu, grad_r, grad_sum, max_sweeps, ws, stats, s);
+    return adj_many_run<float>(grid, M, nprob, r, gamma, u, dJdu, grad_r, grad_sum, max_sweeps, ws, stats, s);
 }

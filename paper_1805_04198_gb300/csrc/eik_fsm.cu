@@ -13,6 +13,7 @@
 #include "engine.cuh"
 #include "host_util.h"
 #include "prof.h"
+#include "ptr_table.cuh"
 
 #include <string>
 #include <vector>
@@ -99,9 +100,9 @@ struct PlainFsmPolicy {
 };
 
 template <class T>
-__global__ void k_fsm_pack(FsmArgs<T> A) {
+__device__ void fsm_pack_body(const FsmArgs<T> &A, size_t bid, size_t nbid) {
     const size_t total = (size_t)A.nx * A.ny;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    for (size_t t = bid * blockDim.x + threadIdx.x; t < total; t += nbid * blockDim.x) {
         int x = (int)(t % A.nx), y = (int)(t / A.nx);
         const size_t gi = (size_t)y * A.sy + x;
         const bool gam = A.gamma[gi] != 0;
@@ -113,8 +114,12 @@ __global__ void k_fsm_pack(FsmArgs<T> A) {
 }
 
 template <class T>
-__global__ void k_fsm_run(FsmArgs<T> A) {
-    extern __shared__ __align__(16) char smem[];
+__global__ void k_fsm_pack(FsmArgs<T> A) {
+    fsm_pack_body(A, blockIdx.x, gridDim.x);
+}
+
+template <class T>
+__device__ void fsm_run_body(const FsmArgs<T> &A, char *smem) {
     Box<T, 1> bx;
     bx.u = A.state;
     bx.st[0] = A.rsk;
@@ -135,6 +140,12 @@ __global__ void k_fsm_run(FsmArgs<T> A) {
     }
 }
 
+template <class T>
+__global__ void k_fsm_run(FsmArgs<T> A) {
+    extern __shared__ __align__(16) char smem[];
+    fsm_run_body(A, smem);
+}
+
 // Multi-CTA form for grids wider than one CTA's blocks: cooperative launch,
 // hand-offs and control words in global memory.
 template <class T>
@@ -144,8 +155,7 @@ __global__ void k_fsm_init_global(FsmArgs<T> A) {
 }
 
 template <class T>
-__global__ void k_fsm_run_global(FsmArgs<T> A) {
-    extern __shared__ __align__(16) char smem[];
+__device__ void fsm_run_global_body(const FsmArgs<T> &A, char *smem, int cta) {
     Box<T, 1> bx;
     bx.u = A.state;
     bx.st[0] = A.rsk;
@@ -157,27 +167,38 @@ __global__ void k_fsm_run_global(FsmArgs<T> A) {
     PlainFsmPolicy<T> pol{A.h};
     long long sweeps;
     bool conv;
-    engine_run<T, 1, false, true>(bx, pol, A.max_sweeps, smem, sweeps, conv, &A.dev->err, A.ghands, A.gctl);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    engine_run<T, 1, false, true>(bx, pol, A.max_sweeps, smem, sweeps, conv, &A.dev->err, A.ghands, A.gctl, cta);
+    if (cta == 0 && threadIdx.x == 0) {
         A.dev->sweeps = (unsigned long long)sweeps;
         A.dev->converged = conv ? 1 : 0;
     }
 }
 
 template <class T>
-__global__ void k_fsm_unpack(FsmArgs<T> A, eik_fsm_stats *out) {
+__global__ void k_fsm_run_global(FsmArgs<T> A) {
+    extern __shared__ __align__(16) char smem[];
+    fsm_run_global_body(A, smem, (int)blockIdx.x);
+}
+
+template <class T>
+__device__ void fsm_unpack_body(const FsmArgs<T> &A, eik_fsm_stats *out, size_t bid, size_t nbid) {
     const size_t total = (size_t)A.nx * A.ny;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    for (size_t t = bid * blockDim.x + threadIdx.x; t < total; t += nbid * blockDim.x) {
         int x = (int)(t % A.nx), y = (int)(t / A.nx);
         A.u[(size_t)y * A.sy + x] = A.state[box_index(x, y, A.ny)];
     }
-    if (out && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (out && bid == 0 && threadIdx.x == 0) {
         out->sweeps = (int64_t)A.dev->sweeps;
         out->converged = A.dev->converged;
         out->error = A.dev->err;
         out->updates = (int64_t)A.dev->sweeps * A.nx * A.ny;
         out->launches = A.launches;
     }
+}
+
+template <class T>
+__global__ void k_fsm_unpack(FsmArgs<T> A, eik_fsm_stats *out) {
+    fsm_unpack_body(A, out, blockIdx.x, gridDim.x);
 }
 
 struct FsmPlan {
@@ -282,6 +303,175 @@ static int fsm_run(const eik_grid *grid, const FsmPlan &P, const void *r, const 
     return cuda_check(cudaGetLastError(), "fsm launch");
 }
 
+
+// --------------------------------------------------------------------------
+// Many right-hand sides (sources Gamma_p, boundary values g_p) on one grid and
+// one slowness: the per-problem kernels of fsm_run, each launch covering every
+// problem (the multi-CTA sweep form in co-resident groups of problems).
+// --------------------------------------------------------------------------
+template <class T>
+struct FsmMany {
+    FsmArgs<T> A;            // shared fields; the per-problem ones are set by fsm_prob
+    const void *const *tab;  // [3][nprob]: gamma, g, u
+    char *ws0;               // workspace of problem 0; problem p at ws0 + p * per
+    size_t per;
+    size_t o_state, o_rsk, o_ghands, o_gctl, o_dev;  // offsets inside a problem's region
+    int nprob;
+};
+
+template <class T>
+__device__ __forceinline__ FsmArgs<T> fsm_prob(const FsmMany<T> &M, int p) {
+    FsmArgs<T> A = M.A;
+    A.gamma = static_cast<const uint8_t *>(M.tab[p]);
+    A.g = static_cast<const T *>(M.tab[M.nprob + p]);
+    A.u = static_cast<T *>(const_cast<void *>(M.tab[2 * M.nprob + p]));
+    char *b = M.ws0 + (size_t)p * M.per;
+    A.state = reinterpret_cast<T *>(b + M.o_state);
+    A.rsk = reinterpret_cast<T *>(b + M.o_rsk);
+    A.ghands = reinterpret_cast<T *>(b + M.o_ghands);
+    A.gctl = reinterpret_cast<int *>(b + M.o_gctl);
+    A.dev = reinterpret_cast<FsmDev *>(b + M.o_dev);
+    return A;
+}
+
+template <class T>
+__global__ void k_fsmm_pack(FsmMany<T> M) {
+    fsm_pack_body(fsm_prob(M, blockIdx.y), blockIdx.x, gridDim.x);
+}
+
+template <class T>
+__global__ void k_fsmm_run(FsmMany<T> M) {
+    extern __shared__ __align__(16) char smem[];
+    fsm_run_body(fsm_prob(M, blockIdx.x), smem);
+}
+
+template <class T>
+__global__ void k_fsmm_init_global(FsmMany<T> M) {
+    const FsmArgs<T> A = fsm_prob(M, blockIdx.x);
+    engine_global_init(A.gctl, A.nb);
+    if (threadIdx.x == 0) A.dev->err = 0;
+}
+
+// CTA c of the launch serves problem p0 + c / nblk as its CTA c % nblk
+template <class T>
+__global__ void k_fsmm_run_global(FsmMany<T> M, int p0, int nblk) {
+    extern __shared__ __align__(16) char smem[];
+    fsm_run_global_body(fsm_prob(M, p0 + (int)blockIdx.x / nblk), smem, (int)blockIdx.x % nblk);
+}
+
+template <class T>
+__global__ void k_fsmm_unpack(FsmMany<T> M, eik_fsm_stats *out) {
+    fsm_unpack_body(fsm_prob(M, blockIdx.y), out ? out + blockIdx.y : nullptr, blockIdx.x, gridDim.x);
+}
+
+struct FsmManyPlan {
+    FsmPlan P;
+    size_t tab_bytes, per, bytes;
+};
+
+static bool fsm_many_plan(const eik_grid *grid, int nprob, FsmManyPlan &M) {
+    if (nprob < 1 || nprob > 65535) {
+        set_error("nprob = %d out of range [1, 65535]", nprob);
+        return false;
+    }
+    if (!fsm_plan(grid, M.P)) return false;
+    M.tab_bytes = ((size_t)3 * nprob * sizeof(void *) + 255) & ~(size_t)255;
+    M.per = (M.P.bytes + 255) & ~(size_t)255;
+    M.bytes = M.tab_bytes + (size_t)nprob * M.per + 256;
+    return true;
+}
+
+template <class T>
+static int fsm_many_run(const eik_grid *grid, const FsmManyPlan &MP, int nprob, const void *r,
+                        const uint8_t *const *gamma, const void *const *g, void *const *u, int64_t max_sweeps,
+                        void *ws, eik_fsm_stats *stats, cudaStream_t s) {
+    const FsmPlan &P = MP.P;
+    FsmMany<T> M;
+    memset(&M, 0, sizeof(M));
+    FsmArgs<T> &A = M.A;
+    A.r = static_cast<const T *>(r);
+    A.sy = grid->stride[1];
+    A.nx = P.nx;
+    A.ny = P.ny;
+    A.nb = P.nb;
+    A.nstepp = P.nstepp;
+    A.h = (T)grid->h;
+    A.max_sweeps = max_sweeps;
+    // offsets of one problem's region (measured against a dummy base)
+    char *const dummy = reinterpret_cast<char *>(256);
+    FsmArgs<T> L;
+    fsm_layout<T>(P, &L, dummy);
+    M.o_state = reinterpret_cast<char *>(L.state) - dummy;
+    M.o_rsk = reinterpret_cast<char *>(L.rsk) - dummy;
+    M.o_ghands = reinterpret_cast<char *>(L.ghands) - dummy;
+    M.o_gctl = reinterpret_cast<char *>(L.gctl) - dummy;
+    M.o_dev = reinterpret_cast<char *>(L.dev) - dummy;
+    M.tab = static_cast<const void *const *>(ws);
+    M.ws0 = static_cast<char *>(ws) + MP.tab_bytes;
+    M.per = MP.per;
+    M.nprob = nprob;
+
+    int rc, dev, optin = 0, nsm = 0;
+    if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncAttributes fa;
+    if ((rc = cuda_check(cudaFuncGetAttributes(&fa, k_fsmm_run<T>), "func attr"))) return rc;
+    const bool single = (int)P.smem <= optin && P.nb <= 32 && (long long)fa.numRegs * 32 * P.nb <= 65536;
+    const int nblk = (P.nb + P.wpc - 1) / P.wpc;
+    int group = nprob;  // problems per cooperative launch
+    if (!single) {
+        if ((rc = cuda_check(cudaFuncSetAttribute(k_fsmm_run_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)P.gsmem), "smem attr")))
+            return rc;
+        int per_sm = 0;
+        if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsmm_run_global<T>, 32 * P.wpc,
+                                                                          P.gsmem), "occupancy")))
+            return rc;
+        group = std::min(nprob, per_sm * nsm / nblk);
+        if (group < 1) {
+            set_error("grid of %d x %d nodes needs %d co-resident CTAs, the device holds %d", P.nx, P.ny, nblk,
+                      per_sm * nsm);
+            return EIK_EUNSUPPORTED;
+        }
+    } else if ((rc = cuda_check(cudaFuncSetAttribute(k_fsmm_run<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)P.smem), "smem attr"))) {
+        return rc;
+    }
+    // pointer table: gamma, g, u
+    std::vector<const void *> tab((size_t)3 * nprob);
+    for (int p = 0; p < nprob; ++p) {
+        tab[p] = gamma[p];
+        tab[nprob + p] = g[p];
+        tab[2 * nprob + p] = u[p];
+    }
+    int nl = upload_ptrs(const_cast<const void **>(M.tab), tab.data(), 3 * nprob, s);
+    if (nl < 0) return nl;
+    const int ngroups = (nprob + group - 1) / group;
+    nl += 2 + (single ? 1 : 1 + ngroups);
+    A.launches = nl;
+    const size_t total = (size_t)P.nx * P.ny;
+    const dim3 eg((unsigned)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, (size_t)nsm * 16 / nprob + 1)),
+                  (unsigned)nprob);
+    EIK_LAUNCH("fsm_pack", s, k_fsmm_pack<T><<<eg, 256, 0, s>>>(M));
+    if (single) {
+        EIK_LAUNCH("fsm_sweeps", s, k_fsmm_run<T><<<nprob, 32 * P.nb, P.smem, s>>>(M));
+    } else {
+        EIK_LAUNCH("fsm_init", s, k_fsmm_init_global<T><<<nprob, 256, 0, s>>>(M));
+        for (int p0 = 0; p0 < nprob; p0 += group) {
+            int np = std::min(group, nprob - p0);
+            void *args[] = {&M, &p0, const_cast<int *>(&nblk)};
+            int tok = prof_begin("fsm_sweeps", s);
+            rc = cuda_check(cudaLaunchCooperativeKernel((void *)k_fsmm_run_global<T>, np * nblk, 32 * P.wpc, args,
+                                                        P.gsmem, s),
+                            "fsm cooperative launch");
+            prof_end(tok, s);
+            if (rc) return rc;
+        }
+    }
+    EIK_LAUNCH("fsm_unpack", s, k_fsmm_unpack<T><<<eg, 256, 0, s>>>(M, stats));
+    return cuda_check(cudaGetLastError(), "fsm launch");
+}
 }  // namespace eik
 
 using namespace eik;
@@ -349,4 +539,42 @@ extern "C" int eik_fsm(const eik_grid *grid, const void *r, const uint8_t *gamma
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (grid->dtype == EIK_F64) return fsm_run<double>(grid, P, r, gamma, g, u, max_sweeps, ws, stats, s);
     return fsm_run<float>(grid, P, r, gamma, g, u, max_sweeps, ws, stats, s);
+}
+
+extern "C" size_t eik_fsm_many_workspace_size(const eik_grid *grid, int nprob) {
+    FsmManyPlan M;
+    if (!fsm_many_plan(grid, nprob, M)) return 0;
+    return M.bytes;
+}
+
+extern "C" int eik_fsm_many(const eik_grid *grid, int nprob, const void *r, const uint8_t *const *gamma,
+                            const void *const *g, void *const *u, int64_t max_sweeps, void *ws, size_t ws_bytes,
+                            eik_fsm_stats *stats, void *stream) {
+    FsmManyPlan M;
+    if (!fsm_many_plan(grid, nprob, M)) return EIK_EINVAL;
+    if (!r || !gamma || !g || !u || !ws) {
+        set_error("eik_fsm_many: NULL argument");
+        return EIK_EINVAL;
+    }
+    for (int p = 0; p < nprob; ++p) {
+        if (!gamma[p] || !g[p] || !u[p]) {
+            set_error("eik_fsm_many: NULL array of problem %d", p);
+            return EIK_EINVAL;
+        }
+    }
+    if (max_sweeps < 1 || max_sweeps > MAX_SWEEPS || grid->n[1] > MAX_BOX_ROWS) {
+        set_error("max_sweeps must be in [1, %lld] and n[1] <= %d", MAX_SWEEPS, MAX_BOX_ROWS);
+        return EIK_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) & 255) {
+        set_error("workspace must be 256-byte aligned");
+        return EIK_EINVAL;
+    }
+    if (ws_bytes < M.bytes) {
+        set_error("workspace of %zu bytes is smaller than the %zu required", ws_bytes, M.bytes);
+        return EIK_ENOMEM;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grid->dtype == EIK_F64) return fsm_many_run<double>(grid, M, nprob, r, gamma, g, u, max_sweeps, ws, stats, s);
+    return fsm_many_run<float>(grid, M, nprob, r, gamma, g, u, max_sweeps, ws, stats, s);
 }

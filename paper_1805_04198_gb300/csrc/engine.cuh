@@ -363,9 +363,11 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
 // the grid must be co-resident (cooperative launch).  All threads must call it.
 template <class T, int NST, bool HASB, bool GLOBAL = false, class P>
 __device__ void engine_run(const Box<T, NST> &bx, const P &pol, long long max_sweeps, char *smem, long long &sweeps,
-                           bool &converged, int *err, T *ghands = nullptr, int *gctl = nullptr) {
+                           bool &converged, int *err, T *ghands = nullptr, int *gctl = nullptr, int cta = -1) {
     const int nwc = GLOBAL ? (int)(blockDim.x >> 5) : bx.nb;   // warps (blocks) of this CTA
-    const int b0 = GLOBAL ? (int)blockIdx.x * nwc : 0;
+    // multi-CTA form: this CTA's index among the CTAs of the box (blockIdx.x
+    // unless several boxes share the grid)
+    const int b0 = GLOBAL ? (cta >= 0 ? cta : (int)blockIdx.x) * nwc : 0;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const size_t ring_e = (size_t)RROWS * 32, sring_e = (size_t)NST * SRCH * CH * 32;

@@ -7,7 +7,8 @@ no fallback: if libeik.so is missing or cannot be loaded, every call raises.
 Entry points mirror the C names:
     eik_fsm_workspace_size, eik_fsm, eik_dd_workspace_size, eik_dd_solve,
     eik_dd_batched_workspace_size, eik_dd_solve_batched, eik_dd_batched_autotune,
-    eik_last_error, eik_version
+    eik_fsm_many_workspace_size, eik_fsm_many, eik_dd_adjoint_many_workspace_size,
+    eik_dd_adjoint_many, eik_last_error, eik_version
 plus the conveniences :func:`fsm` and :func:`dd_solve`, which allocate the
 workspace and the output with torch and return host-side statistics.
 """
@@ -117,6 +118,16 @@ def load():
         lib.eik_dd_batched_autotune.argtypes = [ctypes.c_int, ctypes.POINTER(Grid), pp, pp, pp,
                                                 ctypes.POINTER(DDParams), pp, ctypes.c_int, vp, ctypes.c_size_t,
                                                 ctypes.POINTER(BatchConfig), ctypes.POINTER(ctypes.c_double), vp]
+        lib.eik_fsm_many_workspace_size.restype = ctypes.c_size_t
+        lib.eik_fsm_many_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.c_int]
+        lib.eik_fsm_many.restype = ctypes.c_int
+        lib.eik_fsm_many.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, vp, pp, pp, pp, ctypes.c_int64, vp,
+                                     ctypes.c_size_t, vp, vp]
+        lib.eik_dd_adjoint_many_workspace_size.restype = ctypes.c_size_t
+        lib.eik_dd_adjoint_many_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.c_int]
+        lib.eik_dd_adjoint_many.restype = ctypes.c_int
+        lib.eik_dd_adjoint_many.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, vp, pp, pp, pp, pp, vp,
+                                            ctypes.c_int64, vp, ctypes.c_size_t, vp, vp]
         lib.eik_profile_enable.restype = ctypes.c_int
         lib.eik_profile_enable.argtypes = [ctypes.c_int]
         lib.eik_profile_collect.restype = ctypes.c_int
@@ -436,6 +447,98 @@ class DDBatch:
         raw = bytes(self.stats_dev.cpu().numpy())
         sz = ctypes.sizeof(DDStats)
         return [_as_dict(DDStats.from_buffer_copy(raw[i * sz:(i + 1) * sz])) for i in range(len(self.u))]
+
+
+# --------------------------------------------------------------------------
+# Many sources on one grid and one slowness
+# --------------------------------------------------------------------------
+def _rows(x):
+    """List of per-problem tensors from a list or a stacked tensor."""
+    return [x[i] for i in range(x.shape[0])] if isinstance(x, torch.Tensor) else list(x)
+
+
+def fsm_many(r, gammas, gs, h, max_sweeps=100000, stream=None, sync=True):
+    """Plain FSM for several source sets on one grid.  gammas, gs: stacked
+    tensors [S, ...] (or lists) with r's shape.  Returns (u [S, ...], stats)."""
+    gl, ggl = _rows(gammas), _rows(gs)
+    for gm, gv in zip(gl, ggl):
+        _check_like(r, gv)
+        if gm.dtype != torch.uint8 or gm.shape != r.shape or not gm.is_contiguous():
+            raise ValueError("each gamma must be contiguous uint8 with r's shape")
+    grid = make_grid(r, h)
+    n = len(gl)
+    lib = load()
+    nbytes = int(lib.eik_fsm_many_workspace_size(ctypes.byref(grid), n))
+    if nbytes == 0:
+        raise EikError(-1, eik_last_error())
+    ws = _workspace(nbytes, r.device)
+    u = torch.empty((n,) + tuple(r.shape), dtype=r.dtype, device=r.device)
+    ul = [u[i] for i in range(n)]
+    st = torch.zeros(ctypes.sizeof(FsmStats) * n, dtype=torch.uint8, device=r.device)
+    wsp, wsn = _aligned(ws)
+    _check(lib.eik_fsm_many(ctypes.byref(grid), n, _ptr(r), _ptr_array(gl), _ptr_array(ggl), _ptr_array(ul),
+                            int(max_sweeps), wsp, wsn, _ptr(st), _stream(stream)))
+    if not sync:
+        return u, st
+    raw = bytes(st.cpu().numpy())
+    sz = ctypes.sizeof(FsmStats)
+    stats = [_as_dict(FsmStats.from_buffer_copy(raw[i * sz:(i + 1) * sz])) for i in range(n)]
+    if any(x["error"] for x in stats):
+        raise EikError(-4, "device-side wait expired")
+    return u, stats
+
+
+def adjoint_many(r, gammas, us, dJdus, h, per_problem=False, max_sweeps=100000, stream=None, sync=True):
+    """Sum over source sets of dJ_p/dr (added in source order) at converged
+    solutions us [S, ...] with dJ_p/du given in dJdus [S, ...].  Returns
+    (grad_sum, per-problem gradients [S, ...] or None, stats)."""
+    gl, ul, dl = _rows(gammas), _rows(us), _rows(dJdus)
+    for gm, uu, dj in zip(gl, ul, dl):
+        _check_like(r, uu, dj)
+        if gm.dtype != torch.uint8 or gm.shape != r.shape or not gm.is_contiguous():
+            raise ValueError("each gamma must be contiguous uint8 with r's shape")
+    grid = make_grid(r, h)
+    n = len(gl)
+    lib = load()
+    nbytes = int(lib.eik_dd_adjoint_many_workspace_size(ctypes.byref(grid), n))
+    if nbytes == 0:
+        raise EikError(-1, eik_last_error())
+    ws = _workspace(nbytes, r.device)
+    gsum = torch.empty_like(r)
+    per = torch.empty((n,) + tuple(r.shape), dtype=r.dtype, device=r.device) if per_problem else None
+    st = torch.zeros(ctypes.sizeof(AdjointStats) * n, dtype=torch.uint8, device=r.device)
+    wsp, wsn = _aligned(ws)
+    gptr = _ptr_array([per[i] for i in range(n)]) if per_problem else None
+    _check(lib.eik_dd_adjoint_many(ctypes.byref(grid), n, _ptr(r), _ptr_array(gl), _ptr_array(ul), _ptr_array(dl),
+                                   gptr, _ptr(gsum), int(max_sweeps), wsp, wsn, _ptr(st), _stream(stream)))
+    if not sync:
+        return gsum, per, st
+    raw = bytes(st.cpu().numpy())
+    sz = ctypes.sizeof(AdjointStats)
+    stats = [_as_dict(AdjointStats.from_buffer_copy(raw[i * sz:(i + 1) * sz])) for i in range(n)]
+    if any(x["error"] for x in stats):
+        raise EikError(-4, "device-side wait expired")
+    return gsum, per, stats
+
+
+class EikonalSolveMany(torch.autograd.Function):
+    """u[s] = Eikonal solution for slowness r and source set s (2-D), all
+    source sets solved together; differentiable in r.  gammas, gs: stacked
+    [S, ny, nx].  backward sums the per-source gradients in the library
+    (eik_dd_adjoint_many), keeping only the forward u."""
+
+    @staticmethod
+    def forward(ctx, r, gammas, gs, h):
+        u, _ = fsm_many(r, gammas, gs, h, sync=False)
+        ctx.save_for_backward(r, gammas, u)
+        ctx.h = h
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        r, gammas, u = ctx.saved_tensors
+        gsum, _, _ = adjoint_many(r, gammas, u, grad_u.contiguous(), ctx.h, sync=False)
+        return gsum, None, None, None
 
 
 def parse_dd_stats(st: torch.Tensor) -> dict:
