@@ -125,20 +125,40 @@ __global__ void k_adj_nodes(AdjArgs<T> A) {
     adj_nodes_body(A, blockIdx.x, gridDim.x);
 }
 
+// Skewed statics in output order: thread e writes element e of every channel
+// ([dir][logical block][step][lane], the inverse of skew_index), so a warp's
+// stores are contiguous; positions outside the box get 0.
 template <class T>
 __device__ void adj_pack_body(const AdjArgs<T> &A, size_t bid, size_t nbid) {
     const size_t n = (size_t)A.nx * A.ny;
     const size_t chan = (size_t)4 * A.nb * A.nstepp * 32;
-    for (size_t t = bid * blockDim.x + threadIdx.x; t < n; t += nbid * blockDim.x) {
-        const int x = (int)(t % A.nx), y = (int)(t / A.nx);
-        const T vals[5] = {A.win[t], A.win[n + t], A.win[2 * n + t], A.win[3 * n + t],
-                           A.dJdu[(size_t)y * A.sy + x]};
-        for (int d = 0; d < 4; ++d) {
-            const size_t si = skew_index(d, x, y, A.nb, A.ny, A.nstepp);
-            for (int c = 0; c < 5; ++c) A.sk[c * chan + si] = vals[c];
+    for (size_t e = bid * blockDim.x + threadIdx.x; e < chan; e += nbid * blockDim.x) {
+        const int l = (int)(e & 31);
+        const size_t row = e >> 5;
+        const int st = (int)(row % A.nstepp);
+        const int q = (int)((row / A.nstepp) % A.nb);
+        const int d = (int)(row / ((size_t)A.nstepp * A.nb));
+        const int sx = dir_sx(d), sy = dir_sy(d);
+        const int x = 32 * (sx > 0 ? q : A.nb - 1 - q) + (sx > 0 ? l : 31 - l);
+        const int lr = st - l;
+        T v0 = T(0), v1 = T(0), v2 = T(0), v3 = T(0), v4 = T(0);
+        if (x < A.nx && lr >= 0 && lr < A.ny) {
+            const int y = sy > 0 ? lr : A.ny - 1 - lr;
+            const size_t t = (size_t)y * A.nx + x;
+            v0 = A.win[t];
+            v1 = A.win[n + t];
+            v2 = A.win[2 * n + t];
+            v3 = A.win[3 * n + t];
+            v4 = A.dJdu[(size_t)y * A.sy + x];
         }
-        A.state[box_index(x, y, A.ny)] = T(0);
+        A.sk[e] = v0;
+        A.sk[chan + e] = v1;
+        A.sk[2 * chan + e] = v2;
+        A.sk[3 * chan + e] = v3;
+        A.sk[4 * chan + e] = v4;
     }
+    const size_t box = (size_t)A.nb * A.ny * 32;
+    for (size_t t = bid * blockDim.x + threadIdx.x; t < box; t += nbid * blockDim.x) A.state[t] = T(0);
 }
 
 template <class T>

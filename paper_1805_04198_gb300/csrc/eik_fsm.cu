@@ -99,17 +99,33 @@ struct PlainFsmPolicy {
     }
 };
 
+// Skewed slowness in output order (the inverse of skew_index, so a warp's
+// stores are contiguous; positions outside the box get 0), then the state:
+// Sec. 1.1 initialisation, Gamma fixed at g, everything else large.
 template <class T>
 __device__ void fsm_pack_body(const FsmArgs<T> &A, size_t bid, size_t nbid) {
+    const size_t chan = (size_t)4 * A.nb * A.nstepp * 32;
+    for (size_t e = bid * blockDim.x + threadIdx.x; e < chan; e += nbid * blockDim.x) {
+        const int l = (int)(e & 31);
+        const size_t row = e >> 5;
+        const int st = (int)(row % A.nstepp);
+        const int q = (int)((row / A.nstepp) % A.nb);
+        const int d = (int)(row / ((size_t)A.nstepp * A.nb));
+        const int sx = dir_sx(d), sy = dir_sy(d);
+        const int x = 32 * (sx > 0 ? q : A.nb - 1 - q) + (sx > 0 ? l : 31 - l);
+        const int lr = st - l;
+        T v = T(0);
+        if (x < A.nx && lr >= 0 && lr < A.ny) {
+            const size_t gi = (size_t)(sy > 0 ? lr : A.ny - 1 - lr) * A.sy + x;
+            v = A.gamma[gi] ? T(-1) : A.r[gi];
+        }
+        A.rsk[e] = v;
+    }
     const size_t total = (size_t)A.nx * A.ny;
     for (size_t t = bid * blockDim.x + threadIdx.x; t < total; t += nbid * blockDim.x) {
         int x = (int)(t % A.nx), y = (int)(t / A.nx);
         const size_t gi = (size_t)y * A.sy + x;
-        const bool gam = A.gamma[gi] != 0;
-        const T rv = gam ? T(-1) : A.r[gi];
-        for (int d = 0; d < 4; ++d) A.rsk[skew_index(d, x, y, A.nb, A.ny, A.nstepp)] = rv;
-        // Sec. 1.1 initialisation: Gamma fixed at g, everything else large
-        A.state[box_index(x, y, A.ny)] = gam ? A.g[gi] : Num<T>::inf();
+        A.state[box_index(x, y, A.ny)] = A.gamma[gi] ? A.g[gi] : Num<T>::inf();
     }
 }
 
