@@ -213,28 +213,10 @@ __device__ __forceinline__ void k_step4_body(const DDArgs<T> &A, char *smem, int
     if (*A.done) return;
     const DDGeom &G = A.G;
     const GridDesc d = grid_desc(G, gidx);
-    const T INF = Num<T>::inf();
     const T Hs = T(G.H);
     const size_t n = (size_t)d.nb * d.my * 32;
     T *U = A.U + d.off;
-    // C_H(nbrs^H(U^k)) from the previous iterate; keep U^k for the delta
-    for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
-        int b = (int)(e / ((size_t)d.my * 32));
-        int rem = (int)(e % ((size_t)d.my * 32));
-        int j = rem / 32, i = 32 * b + rem % 32;
-        if (i >= d.mx) continue;
-        const size_t a = d.off + e;
-        A.Uprev[a] = U[e];
-        T vmx = i > 0 ? U[box_index(i - 1, j, d.my)] : INF;
-        T vpx = i + 1 < d.mx ? U[box_index(i + 1, j, d.my)] : INF;
-        T vmy = j > 0 ? U[box_index(i, j - 1, d.my)] : INF;
-        T vpy = j + 1 < d.my ? U[box_index(i, j + 1, d.my)] : INF;
-        const T rv = A.rc[a];
-        const T cold = local_solve2_value(vmx, vpx, vmy, vpy, Num<T>::mul(rv > T(0) ? rv : T(0), Hs));
-        T *sk = A.cold_sk + d.skoff;
-        for (int dd = 0; dd < 4; ++dd) sk[skew_index(dd, i, j, d.nb, d.my, d.nstepp)] = cold;
-    }
-    __syncthreads();
+    // C_H(nbrs^H(U^k)), U^k and W = w^k were prepared by Alg. 4 (alg4_body)
     // "Initialize U as described in Sec. 1.1"
     for (size_t e = threadIdx.x; e < n; e += blockDim.x) U[e] = A.U0[d.off + e];
     __threadfence_block();
@@ -258,8 +240,6 @@ __device__ __forceinline__ void k_step4_body(const DDArgs<T> &A, char *smem, int
         if (!conv) atomicAdd(&A.st->coarse_caps, 1ull);
         atomicAdd(&A.st->coarse_updates, (unsigned long long)sweeps * d.mx * d.my);
     }
-    // W = w^k
-    for (size_t e = threadIdx.x; e < n; e += blockDim.x) A.W[d.off + e] = A.wk[d.off + e];
 }
 
 // --------------------------------------------------------------------------
@@ -666,10 +646,24 @@ __device__ void alg4_body(const DDArgs<T> &A, size_t bid, size_t nbid) {
         if (!onx || (wkx >= 0 && Wx >= 0)) m |= 4;
         if (!ony || (wky <= 0 && Wy <= 0)) m |= 8;
         if (!ony || (wky >= 0 && Wy >= 0)) m |= 16;
+        // Step 4 inputs that depend only on U^k, computed here while U still
+        // holds U^k: C_H(nbrs^H(U^k)) of the node's own shifted grid, U^k for
+        // the delta, and W = w^k (the mask above has read W^k)
+        const T INF = Num<T>::inf();
+        const T *Ug = A.U + d.off;
+        const T vmx = i > 0 ? Ug[box_index(i - 1, j, d.my)] : INF;
+        const T vpx = i + 1 < d.mx ? Ug[box_index(i + 1, j, d.my)] : INF;
+        const T vmy = j > 0 ? Ug[box_index(i, j - 1, d.my)] : INF;
+        const T vpy = j + 1 < d.my ? Ug[box_index(i, j + 1, d.my)] : INF;
+        const T rv = A.rc[a];
+        const T cold = local_solve2_value(vmx, vpx, vmy, vpy, Num<T>::mul(rv > T(0) ? rv : T(0), T(G.H)));
+        A.Uprev[a] = A.U[a];
+        A.W[a] = wkv;
         for (int dd = 0; dd < 4; ++dd) {
             size_t si = d.skoff + skew_index(dd, i, j, d.nb, d.my, d.nstepp);
             A.uk_sk[si] = ukv;
             A.mask_sk[si] = m;
+            A.cold_sk[si] = cold;
         }
     }
 }

@@ -7,10 +7,11 @@
 //            the converged state at the subdomain's coarse-set nodes (written
 //            as per-subdomain copies) and the fine values of interior nodes;
 //   k_alg4   one thread per coarse-set node: Alg. 4 choice among the copies
-//            -> u^k, w^k; the skewed per-direction inputs of Alg. 5;
+//            -> u^k, w^k; the skewed per-direction inputs of Alg. 5 (u^k,
+//            agreement mask, C_H(nbrs U^k)), U^k for the delta, W = w^k;
 //   k_check  stop test (k == max_iter, or k >= 1 and max|U^k - U^{k-1}| < tol);
-//   k_step4  one CTA per shifted coarse grid: C_H(nbrs U^k), reset, Alg. 5
-//            sweeps by the same engine, W = w^k;
+//   k_step4  one CTA per shifted coarse grid: reset, Alg. 5 sweeps by the
+//            same engine;
 //   k_causal cooperative: Alg. 2 along every coarse line to its least fixed
 //            point (segmented max-scans, rounds until nothing changes);
 //   k_delta  max|U^{k+1} - U^k| over the coarse set.
