@@ -509,6 +509,45 @@ def run_extra(args):
         kern = ("dd3_fine_subdomains", st["fine_updates"] * BYTES_PER_UPDATE_F32 / (fine_ms / 1e3) / 1e9)
         extra = {"dd_stats": {k: st[k] for k in ("iters", "fsm_sweeps_max", "fine_updates", "coarse_updates")},
                  "kernel_ms": {k: v["total_ms"] for k, v in prof.items()}}
+        # accuracy against the FP64 full-grid FSM (the discrete solution) and the
+        # plain FP32 full-grid FSM at equal error (not part of the timed steps)
+        try:
+            uf, fst = eik.fsm(R.double(), G, g.double(), w["h"])
+            fin = torch.isfinite(uf)
+            umax = uf[fin].abs().max().item()
+
+            def rel_err(x):
+                return (x.double() - uf)[fin].abs().max().item() / umax
+
+            dd_err = rel_err(u)
+
+            def fsm_timed(ms_):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(0.0)
+                e0.record(stream)
+                uu, ss = eik.fsm(R, G, g, w["h"], max_sweeps=ms_, sync=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                return uu, e0.elapsed_time(e1), eik.FsmStats.from_buffer_copy(bytes(ss.cpu().numpy())).sweeps
+
+            lo, hi = 1, fst["sweeps"]
+            while lo < hi:
+                mid = (lo + hi) // 2
+                uu, _, _ = fsm_timed(mid)
+                if rel_err(uu) <= dd_err:
+                    hi = mid
+                else:
+                    lo = mid + 1
+            uu_eq, t_eq, _ = fsm_timed(lo)
+            uu_full, t_full, full_sweeps = fsm_timed(100000)
+            extra["accuracy"] = {"rel_max_err_vs_fp64_fsm": dd_err, "fp64_fsm_sweeps": fst["sweeps"]}
+            extra["fsm_baseline_f32"] = {"sweeps_to_equal_error": lo, "time_to_equal_error_ms": t_eq,
+                                         "rel_max_err_at_equal": rel_err(uu_eq), "converged_sweeps": full_sweeps,
+                                         "time_to_convergence_ms": t_full,
+                                         "rel_max_err_converged": rel_err(uu_full),
+                                         "dd_over_fsm_time_at_equal_error": ms / t_eq}
+        except Exception as e:  # noqa: BLE001
+            extra["fsm_baseline_f32"] = {"unavailable": str(e)[:160]}
         hr = torch.from_numpy(w["r"].astype(np.float32)).pin_memory()
         hu = torch.empty_like(hr).pin_memory()
         def e2e_step():

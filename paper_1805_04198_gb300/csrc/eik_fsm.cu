@@ -526,7 +526,15 @@ extern "C" int eik_profile_collect(eik_kernel_time *out, int max_entries) {
     return (int)acc.size();
 }
 
+namespace eik {
+// 3-D form (eik_fsm3.cu)
+size_t fsm3_workspace_size(const eik_grid *grid);
+int fsm3_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, void *u, int64_t max_sweeps,
+             void *ws, eik_fsm_stats *stats, cudaStream_t s);
+}  // namespace eik
+
 extern "C" size_t eik_fsm_workspace_size(const eik_grid *grid) {
+    if (grid && grid->ndim == 3) return valid_grid_common(grid, 3) ? fsm3_workspace_size(grid) : 0;
     FsmPlan P;
     if (!fsm_plan(grid, P)) return 0;
     return P.bytes;
@@ -534,6 +542,27 @@ extern "C" size_t eik_fsm_workspace_size(const eik_grid *grid) {
 
 extern "C" int eik_fsm(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, void *u,
                        int64_t max_sweeps, void *ws, size_t ws_bytes, eik_fsm_stats *stats, void *stream) {
+    if (grid && grid->ndim == 3) {
+        if (!valid_grid_common(grid, 3)) return EIK_EINVAL;
+        if (!r || !gamma || !g || !u || !ws) {
+            set_error("eik_fsm: NULL array argument");
+            return EIK_EINVAL;
+        }
+        if (max_sweeps < 1 || max_sweeps > MAX_SWEEPS) {
+            set_error("max_sweeps must be in [1, %lld]", MAX_SWEEPS);
+            return EIK_EINVAL;
+        }
+        if (reinterpret_cast<uintptr_t>(ws) & 255) {
+            set_error("workspace must be 256-byte aligned");
+            return EIK_EINVAL;
+        }
+        const size_t need = fsm3_workspace_size(grid);
+        if (ws_bytes < need) {
+            set_error("workspace of %zu bytes is smaller than the %zu required", ws_bytes, need);
+            return EIK_ENOMEM;
+        }
+        return fsm3_run(grid, r, gamma, g, u, max_sweeps, ws, stats, static_cast<cudaStream_t>(stream));
+    }
     FsmPlan P;
     if (!fsm_plan(grid, P)) return EIK_EINVAL;
     if (!r || !gamma || !g || !u || !ws) {

@@ -257,6 +257,37 @@ def test_dd_full_size_fixed_point_property(gpu):
     assert rel.max() <= TOL32
 
 
+@pytest.mark.parametrize("shape", [(17, 20, 23), (33, 33, 33), (9, 40, 12)])
+def test_fsm3_fp64_bitwise(gpu, shape):
+    """3-D full-grid FSM (hyperplane sweeps over the whole grid): bitwise equal
+    to the oracle's serial loop nest."""
+    r, gamma, g = _random_problem(shape, sum(shape))
+    u_ref, s_ref, c_ref = O.fsm(r, gamma, g, 0.05)
+    u, st = gpu.fsm(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), 0.05)
+    assert c_ref and st["converged"] == 1 and st["sweeps"] == s_ref
+    np.testing.assert_array_equal(u.cpu().numpy(), u_ref)
+
+
+def test_fsm3_sweep_cap_matches_oracle(gpu):
+    r, gamma, g = _random_problem((21, 18, 25), 3, nsrc=1)
+    for k in (1, 2, 5):
+        u_ref, s_ref, _ = O.fsm(r, gamma, g, 0.05, max_sweeps=k)
+        u, st = gpu.fsm(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), 0.05, max_sweeps=k)
+        assert st["sweeps"] == s_ref == k
+        np.testing.assert_array_equal(u.cpu().numpy(), u_ref)
+
+
+def test_fsm3_fp32_against_oracle(gpu):
+    n = 65
+    h = 1.0 / (n - 1)
+    r = I.sin_product((n, n, n), h, 0.4, 0.25).astype(np.float32)
+    gamma, g = I.point_source((n, n, n), (n // 2, n // 3, n // 4))
+    u_ref, _, _ = O.fsm(r.astype(np.float64), gamma, g, h)
+    u, st = gpu.fsm(_t(r, torch.float32), _t(gamma, torch.uint8), _t(g, torch.float32), h)
+    assert st["converged"] == 1
+    assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
+
+
 def _dd3_case(n, amp=0.4, eps=0.25, src=None):
     h = 1.0 / (n - 1)
     r = I.sin_product((n, n, n), h, amp, eps)
