@@ -12,6 +12,7 @@ Functions (each follows the paper section named in its docstring):
   dd           two-scale domain decomposition, Sec. 3.2 Steps 1-4, Alg. 1-5
   adjoint      discrete adjoint of the converged Godunov system (no paper
                counterpart; checked by finite differences)
+  theta_estimate  per-node weight of Sec. 4.2 (eqs. secthetaest, thetaest)
 """
 from __future__ import annotations
 
@@ -46,7 +47,10 @@ class DDParams(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_long * 3), ("h", ctypes.c_double),
                 ("tiles", ctypes.c_int * 3), ("c", ctypes.c_int), ("theta", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_fsm_sweeps", ctypes.c_long), ("max_coarse_sweeps", ctypes.c_long)]
+                ("max_fsm_sweeps", ctypes.c_long), ("max_coarse_sweeps", ctypes.c_long),
+                ("theta_adaptive", ctypes.c_int), ("omega", ctypes.c_double * 3),
+                ("sig_gamma", ctypes.c_double), ("sig_delta", ctypes.c_double), ("sig_x0", ctypes.c_double),
+                ("theta_cap", ctypes.c_double)]
 
 
 class DDStats(ctypes.Structure):
@@ -79,6 +83,9 @@ def _load():
             lib.orc_fmm.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp]
             lib.orc_dd.restype = ctypes.c_int
             lib.orc_dd.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, dp, dp, ctypes.POINTER(DDStats)]
+            lib.orc_theta_estimate.restype = ctypes.c_double
+            lib.orc_theta_estimate.argtypes = [ctypes.POINTER(DDParams), ctypes.c_double, dp, ctypes.c_int,
+                                               ctypes.c_double]
             lib.orc_adjoint.restype = None
             lib.orc_adjoint.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, dp]
             _lib = lib
@@ -150,18 +157,24 @@ def fmm(r, gamma, g, h):
 
 
 def dd(r, gamma, g, h, tiles, c, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
-       max_coarse_sweeps=80, return_coarse=False):
+       max_coarse_sweeps=80, return_coarse=False, theta_adaptive=False, omega=(1.0, 1.0, 1.0),
+       sig_gamma=0.75, sig_delta=0.01, sig_x0=0.9, theta_cap=0.0):
     """Two-scale DD iteration (Sec. 3.2, Steps 1-4).
 
     tiles: subdomains per axis in (x, y[, z]) order.  Returns (u, stats dict,
-    delta_log[, U]) where delta_log[k] = max |U^k - U^{k-1}|.
+    delta_log[, U]) where delta_log[k] = max |U^k - U^{k-1}|.  With
+    theta_adaptive the weight of Alg. 5 is estimated per node (Sec. 4.2, eq.
+    secthetaest damped by eq. thetaest; omega, sig_* its parameters) and
+    `theta` is used where the estimate is undefined.
     """
     lib = _load()
     r, gamma, g = _prep(r, gamma, g)
     d, n = _shape_n(r.shape)
     t = list(tiles) + [1] * (3 - len(tiles))
     p = DDParams(d, n, float(h), (ctypes.c_int * 3)(*t), int(c), float(theta), int(max_iter), float(tol),
-                 int(max_fsm_sweeps), int(max_coarse_sweeps))
+                 int(max_fsm_sweeps), int(max_coarse_sweeps), 1 if theta_adaptive else 0,
+                 (ctypes.c_double * 3)(*omega), float(sig_gamma), float(sig_delta), float(sig_x0),
+                 float(theta_cap))
     u = np.empty_like(r)
     U = np.empty_like(r)
     log = np.empty(max_iter + 1, dtype=np.float64)
@@ -173,6 +186,18 @@ def dd(r, gamma, g, h, tiles, c, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps
     if return_coarse:
         out = out + (U,)
     return out
+
+
+def theta_estimate(du, dC, omega=(1.0, 1.0, 1.0), sig_gamma=0.75, sig_delta=0.01, sig_x0=0.9, theta_cap=0.0,
+                   fallback=0.2):
+    """Per-node weight of Sec. 4.2 from du = u^k - u^{k-1} and the last changes
+    dC[s] of the coarse solver (eq. secthetaest, damping of eq. thetaest)."""
+    lib = _load()
+    p = DDParams(2, (ctypes.c_long * 3)(1, 1, 1), 1.0, (ctypes.c_int * 3)(1, 1, 1), 1, float(fallback), 0, 0.0, 1, 1,
+                 1, (ctypes.c_double * 3)(*omega), float(sig_gamma), float(sig_delta), float(sig_x0),
+                 float(theta_cap))
+    a = np.ascontiguousarray(dC, dtype=np.float64)
+    return lib.orc_theta_estimate(ctypes.byref(p), float(du), _dp(a), len(a), float(fallback))
 
 
 def adjoint(r, gamma, u, dJdu, h):

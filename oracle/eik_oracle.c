@@ -482,23 +482,80 @@ static long step1_grid(const geom_t *G, const long *o, double H, const double *r
     return s;
 }
 
+/* Per-node weight of Sec. 4.2.  The bound M-bar of Theorem 2 is estimated by
+ * eq. secthetaest: the last change of the fine values over a weighted mean of
+ * the last changes of the coarse solver,
+ *   theta-bar = (u^k - u^{k-1}) / [sum_s w_s (C^{k-s} - C^{k-1-s}) / sum_s w_s],
+ * C^m = C_H(nbrs^H(U^m)), over the terms s = 0, 1, 2 whose iterates exist
+ * (reading: the lag of the first estimate, eq. firstthetaest, for every term),
+ * then damped by eq. thetaest: [sig t + (1 - sig) delta t]^+ with
+ * sig = 1 / (1 + exp((t - x0) / gamma)).  Undefined estimates (no history,
+ * zero or non-finite quotient) take the constant theta. */
+typedef struct {
+    const orc_dd_params *p;
+    int nhist;               /* coarse-solver values available before this update */
+    const double *C1, *C2, *C3;  /* C^{k-1}, C^{k-2}, C^{k-3} (full grid) */
+    const double *uprev;     /* u^{k-1} */
+} theta_ctx;
+
+/* The estimate itself: du = u^k - u^{k-1}, dC[s] = C^{k-s} - C^{k-1-s} for the
+ * n available terms.  Returns `fallback` where the estimate is undefined. */
+double orc_theta_estimate(const orc_dd_params *p, double du, const double *dC, int n, double fallback)
+{
+    double den = 0.0, wsum = 0.0, t, sig, v;
+    int s;
+    for (s = 0; s < n && s < 3; ++s) {
+        den += p->omega[s] * dC[s];
+        wsum += p->omega[s];
+    }
+    if (!(wsum > 0.0)) return fallback;
+    den = den / wsum;
+    t = du / den;
+    if (!isfinite(t) || den == 0.0) return fallback;
+    sig = 1.0 / (1.0 + exp((t - p->sig_x0) / p->sig_gamma));
+    v = sig * t + (1.0 - sig) * p->sig_delta * t;
+    if (p->theta_cap > 0.0 && v > p->theta_cap) v = p->theta_cap;
+    return v > 0.0 ? v : 0.0;
+}
+
+static double theta_node(const theta_ctx *T, long f, double uk_f, double Ck_f)
+{
+    const orc_dd_params *p = T->p;
+    const double *Cs[4];
+    double dC[3];
+    int s, n;
+    if (!p->theta_adaptive || T->nhist < 1) return p->theta;
+    Cs[1] = T->C1;
+    Cs[2] = T->C2;
+    Cs[3] = T->C3;
+    n = T->nhist < 3 ? T->nhist : 3;
+    for (s = 0; s < n; ++s) dC[s] = ((s == 0) ? Ck_f : Cs[s][f]) - Cs[s + 1][f];
+    return orc_theta_estimate(p, uk_f - T->uprev[f], dC, n, p->theta);
+}
+
 /* Step 4 on one shifted grid: Alg. 5.  Uk = U^k (for C_H(nbrs U^k)), uk/wk the
- * Alg. 4 output, Wk = W^k.  Writes the swept U; W is set to w^k by the caller. */
+ * Alg. 4 output, Wk = W^k.  Writes the swept U (W is set to w^k by the caller)
+ * and C_H(nbrs U^k) at the grid's nodes into Cout (full grid, may be NULL).
+ * The weight of a node is theta_node(T, ...) (T may be NULL: constant theta). */
 static long step4_grid(const geom_t *G, const long *o, double H, double theta, const double *r,
                        const unsigned char *gamma, const double *g, const double *Uk, const double *uk,
-                       const signed char *wk, const signed char *Wk, double *U, long max_sweeps, long *caps)
+                       const signed char *wk, const signed char *Wk, double *U, long max_sweeps, long *caps,
+                       const theta_ctx *T, double *Cout)
 {
     long m[3], M, s = 0, x, y, z;
     int nq = 1 << G->d, d = G->d;
-    double *Ul, *Ukl, *Cold, *ukl, *rl;
+    double *Ul, *Ukl, *Cold, *ukl, *rl, *thl;
     unsigned char *fl;
     int *Al;
+    long *fidx;
     signed char *wkl, *Wkl;
     grid_box(G, o, m);
     M = m[0] * m[1] * m[2];
     Ul = malloc(sizeof(double) * (size_t)M);
     Ukl = malloc(sizeof(double) * (size_t)M);
     Cold = malloc(sizeof(double) * (size_t)M);
+    thl = malloc(sizeof(double) * (size_t)M);
+    fidx = malloc(sizeof(long) * (size_t)M);
     ukl = malloc(sizeof(double) * (size_t)M);
     rl = malloc(sizeof(double) * (size_t)M);
     fl = malloc((size_t)M);
@@ -512,6 +569,7 @@ static long step4_grid(const geom_t *G, const long *o, double H, double theta, c
                 int k;
                 coords(G, f, xf);
                 rl[l] = r[f];
+                fidx[l] = f;
                 fl[l] = gamma[f] ? 1 : 0;
                 Ukl[l] = Uk[f];
                 ukl[l] = uk[f];
@@ -532,6 +590,8 @@ static long step4_grid(const geom_t *G, const long *o, double H, double theta, c
                 signed char w[3];
                 nbrs(d, m, Ukl, x, y, z, vm, vp);
                 Cold[l] = orc_local_solve(d, vm, vp, rl[l] * H, w);
+                thl[l] = T ? theta_node(T, fidx[l], ukl[l], Cold[l]) : theta;
+                if (Cout) Cout[fidx[l]] = Cold[l];
             }
     for (;;) {
         int changed = 0, sg[3];
@@ -560,7 +620,7 @@ static long step4_grid(const geom_t *G, const long *o, double H, double theta, c
                         if (!((a <= 0 && b <= 0 && c <= 0) || (a >= 0 && b >= 0 && c >= 0))) pass = 0;
                     }
                     if (pass)
-                        Unew = ukl[l] + theta * (Ut - Cold[l]);
+                        Unew = ukl[l] + thl[l] * (Ut - Cold[l]);
                     else
                         Unew = ukl[l];
                     if (!(Unew == Ul[l])) changed = 1;
@@ -573,6 +633,8 @@ static long step4_grid(const geom_t *G, const long *o, double H, double theta, c
     free(Ul);
     free(Ukl);
     free(Cold);
+    free(thl);
+    free(fidx);
     free(ukl);
     free(rl);
     free(fl);
@@ -753,10 +815,11 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     long i, ntiles;
     int k, it;
     double H, delta = INF;
-    double *U, *Uprev, *uk, **tu;
+    double *U, *Uprev, *uk, **tu, *uprev, *Chist[4];
     signed char *W, *wk, **tw;
     long tilenodes;
     orc_dd_stats S0;
+    theta_ctx tctx;
     memset(&S0, 0, sizeof(S0));
     if (p->d < 2 || p->d > 3 || p->c < 1) return -1;
     memset(&G, 0, sizeof(G));
@@ -784,6 +847,8 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     U = malloc(sizeof(double) * (size_t)G.N);
     Uprev = malloc(sizeof(double) * (size_t)G.N);
     uk = malloc(sizeof(double) * (size_t)G.N);
+    uprev = malloc(sizeof(double) * (size_t)G.N);
+    for (k = 0; k < 4; ++k) Chist[k] = malloc(sizeof(double) * (size_t)G.N);
     W = calloc((size_t)(3 * G.N), 1);
     wk = calloc((size_t)(3 * G.N), 1);
     tu = malloc(sizeof(double *) * (size_t)ntiles);
@@ -841,6 +906,12 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
         }
         /* Step 4: Alg. 5 on every shifted grid, W = w^k, then the causal sweep. */
         memcpy(Uprev, U, sizeof(double) * (size_t)G.N);
+        tctx.p = p;
+        tctx.nhist = it < 3 ? it : 3;
+        tctx.C1 = it >= 1 ? Chist[(it + 3) % 4] : NULL;
+        tctx.C2 = it >= 2 ? Chist[(it + 2) % 4] : NULL;
+        tctx.C3 = it >= 3 ? Chist[(it + 1) % 4] : NULL;
+        tctx.uprev = uprev;
         {
             long o[3];
             int first = 1;
@@ -850,7 +921,7 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
                 long s;
                 first = 0;
                 s = step4_grid(&G, o, H, p->theta, r, gamma, g, Uprev, uk, wk, W, Unew, p->max_coarse_sweeps,
-                               &S0.coarse_cap_hits);
+                               &S0.coarse_cap_hits, &tctx, Chist[it % 4]);
                 if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
                 {
                     long m[3];
@@ -875,6 +946,7 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
         }
         delta = coarse_delta(&G, U, Uprev);
         if (delta_log && it + 1 <= p->max_iter) delta_log[it + 1] = delta;
+        memcpy(uprev, uk, sizeof(double) * (size_t)G.N);
     }
     S0.last_delta = delta;
 
@@ -908,6 +980,8 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     free(tw);
     free(U);
     free(Uprev);
+    free(uprev);
+    for (k = 0; k < 4; ++k) free(Chist[k]);
     free(uk);
     free(W);
     free(wk);

@@ -52,6 +52,13 @@ typedef struct {
     double tol;           /* stop when max |U^k - U^{k-1}| < tol (k >= 1) */
     long max_fsm_sweeps;  /* per fine subdomain solve */
     long max_coarse_sweeps; /* per coarse grid solve (Step 1 and Step 4) */
+    /* Per-node theta (Sec. 4.2, eq. secthetaest with the damping of eq.
+     * thetaest) when theta_adaptive != 0; `theta` is then the value used
+     * where the estimate is undefined (first update, non-finite quotient). */
+    int theta_adaptive;
+    double omega[3];      /* weights of the last three coarse-solver changes */
+    double sig_gamma, sig_delta, sig_x0;  /* gamma, delta, x_0 of eq. thetaest */
+    double theta_cap;     /* upper bound on the damped estimate (<= 0: none) */
 } orc_dd_params;
 
 typedef struct {
@@ -76,6 +83,12 @@ typedef struct {
  *   delta_log (nullable) max_iter+1 entries: delta_log[k] = max|U^k - U^{k-1}|
  *             (delta_log[0] = inf).
  * Returns 0 on success, -1 on invalid parameters. */
+/* Per-node weight estimate of Sec. 4.2 (eq. secthetaest damped by eq.
+ * thetaest, capped at p->theta_cap when positive): du = u^k - u^{k-1},
+ * dC[s] = C_H(nbrs U^{k-s}) - C_H(nbrs U^{k-1-s}), s < n (n <= 3).  Returns
+ * `fallback` when the quotient is undefined (no term, zero or non-finite). */
+double orc_theta_estimate(const orc_dd_params *p, double du, const double *dC, int n, double fallback);
+
 int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
            double *u_out, double *U_out, double *delta_log, orc_dd_stats *st);
 

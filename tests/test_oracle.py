@@ -288,3 +288,55 @@ def test_dd3_single_subdomain_is_fsm_and_converges():
     u, st, _ = O.dd(r, gamma, 0.0, h, (4, 4, 4), 4, theta=0.2, max_iter=40, tol=1e-12, max_coarse_sweeps=16)
     assert st["converged"] == 1
     assert np.max(np.abs(u - uf)) < 1e-10 * np.max(uf)
+
+
+# --------------------------------------------------------------------------
+# Per-node weight of Sec. 4.2 (eq. secthetaest damped by eq. thetaest)
+# --------------------------------------------------------------------------
+def test_theta_estimate_shape():
+    """Properties the damping fixes whatever the rounding: at the midpoint
+    t = x0 the sigmoid is exactly 1/2; the damped value lies between delta*t
+    and t and tends to delta*t; negative estimates give 0; undefined ones the
+    fallback; the weighted mean of the coarse-solver changes; the cap."""
+    x0, dl = 0.9, 0.01
+    # t = du / mean(dC) = x0 exactly
+    v = O.theta_estimate(x0 * 0.5, [0.5], sig_x0=x0, sig_delta=dl)
+    assert abs(v - 0.5 * (x0 + dl * x0)) <= 1e-15
+    for t in (0.05, 0.3, 2.0, 7.5):
+        v = O.theta_estimate(t, [1.0])
+        assert dl * t < v < t
+    assert abs(O.theta_estimate(400.0, [1.0]) / 400.0 - dl) < 1e-12
+    assert O.theta_estimate(-0.3, [1.0]) == 0.0
+    assert O.theta_estimate(0.3, [0.0], fallback=0.17) == 0.17
+    assert O.theta_estimate(0.3, [], fallback=0.17) == 0.17
+    assert O.theta_estimate(np.inf, [1.0], fallback=0.17) == 0.17
+    # mean over the three terms; weights select terms
+    assert O.theta_estimate(0.3, [0.5, 1.0, 1.5]) == O.theta_estimate(0.3, [1.0])
+    assert O.theta_estimate(0.3, [1.0, 7.0, -3.0], omega=(1.0, 0.0, 0.0)) == O.theta_estimate(0.3, [1.0])
+    assert O.theta_estimate(400.0, [1.0], theta_cap=1.0) == 1.0
+
+
+def test_dd_adaptive_theta_first_update_and_theorem1():
+    """The first weighted update has no history and uses the constant theta,
+    so one iteration equals the constant-theta run bitwise; Theorem 1's
+    exactness (U^k = u^f on columns i <= k) holds for any weights, adaptive
+    ones included."""
+    n = 65
+    h = 1.0 / (n - 1)
+    xs = np.arange(n) * h
+    r = 1.0 + 0.5 * np.sin(8 * np.pi * xs)[None, :] * np.sin(8 * np.pi * xs)[:, None]
+    gamma = np.zeros((n, n), np.uint8)
+    gamma[20, 40] = 1
+    g = np.zeros((n, n))
+    a, _, _ = O.dd(r, gamma, g, h, (4, 4), 8, theta=0.2, max_iter=1, max_coarse_sweeps=8)
+    b, _, _ = O.dd(r, gamma, g, h, (4, 4), 8, theta=0.2, max_iter=1, max_coarse_sweeps=8, theta_adaptive=True,
+                   theta_cap=1.0)
+    np.testing.assert_array_equal(a, b)
+    N, M = 8, 8
+    r, gamma, g, h = _model_problem(N, M)
+    uf, _, _ = O.fsm(r, gamma, g, h)
+    for k in (2, 5, N):
+        _, _, _, U = O.dd(r, gamma, g, h, (N, 1), M, theta=0.5, max_iter=k, tol=-1.0, return_coarse=True,
+                          theta_adaptive=True, theta_cap=1.0)
+        for i in range(k + 1):
+            assert np.array_equal(U[1:, i * M], uf[1:, i * M]), (k, i)
