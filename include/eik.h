@@ -118,6 +118,16 @@ typedef struct {
     double tol;            /* stop once k >= 1 and max|U^k - U^{k-1}| < tol */
     int64_t max_fsm_sweeps;    /* cap per subdomain solve (Step 3) */
     int64_t max_coarse_sweeps; /* cap per coarse-grid solve (Steps 1 and 4) */
+    /* Per-node weight (Sec. 4.2) instead of the constant theta when
+     * theta_adaptive != 0 (2-D single-problem solves): the bound of Theorem 2
+     * estimated by eq. secthetaest, (u^k - u^{k-1}) over the weighted mean of
+     * the last (up to three) changes of C_H(nbrs U), damped by eq. thetaest
+     * [s t + (1 - s) delta t]^+ with s = 1 / (1 + exp((t - x0) / gamma)), and
+     * capped at theta_cap when theta_cap > 0.  theta is used where the
+     * estimate is undefined (first update, zero or non-finite quotient). */
+    int theta_adaptive;
+    double omega[3];           /* weights of the last three coarse-solver changes */
+    double sig_gamma, sig_delta, sig_x0, theta_cap;
 } eik_dd_params;
 
 typedef struct {

@@ -50,6 +50,11 @@ struct DDArgs {
     T theta, tol;
     int max_iter;
     long long max_fsm, max_coarse;
+    // per-node weight of Sec. 4.2 (adaptive theta)
+    int adaptive;
+    double om[3], sg, sd, sx0, cap;
+    T *Ch[4];      // C_H(nbrs^H(U^m)) of the last four iterates m, slot m % 4
+    T *theta_sk;   // skewed per-node weight (a static of the Alg. 5 sweeps)
 };
 
 template <class T>
@@ -83,6 +88,7 @@ struct FsmPolicy {
 template <class T>
 struct Alg5Policy {
     T H, theta;
+    bool per_node;  // weight from the fourth static instead of `theta`
     __device__ __forceinline__ T update(T self, T vmx, T vpx, T vmy, T vpy, const T *sv, uint8_t mask,
                                         bool &changed) const {
         using N = Num<T>;
@@ -93,7 +99,8 @@ struct Alg5Policy {
         bool pass = (Ut < N::inf()) && (cold < N::inf());
         pass = pass && ((wx <= 0 && (mask & 2)) || (wx >= 0 && (mask & 4)));
         pass = pass && ((wy <= 0 && (mask & 8)) || (wy >= 0 && (mask & 16)));
-        const T nu0 = pass ? N::add(uk, N::mul(theta, N::sub(Ut, cold))) : uk;
+        const T th = per_node ? sv[3] : theta;
+        const T nu0 = pass ? N::add(uk, N::mul(th, N::sub(Ut, cold))) : uk;
         const T nu = (mask & 1) ? self : nu0;
         changed = !(nu == self);
         return nu;
@@ -208,8 +215,8 @@ __device__ __forceinline__ void k_step1_body(const DDArgs<T> &A, char *smem, int
 }
 
 // Step 4: Alg. 5 on every shifted grid.
-template <class T>
-__device__ __forceinline__ void k_step4_body(const DDArgs<T> &A, char *smem, int gidx) {
+template <class T, bool ADAPT>
+__device__ __forceinline__ void k_step4_gen(const DDArgs<T> &A, char *smem, int gidx) {
     if (*A.done) return;
     const DDGeom &G = A.G;
     const GridDesc d = grid_desc(G, gidx);
@@ -221,25 +228,36 @@ __device__ __forceinline__ void k_step4_body(const DDArgs<T> &A, char *smem, int
     for (size_t e = threadIdx.x; e < n; e += blockDim.x) U[e] = A.U0[d.off + e];
     __threadfence_block();
     __syncthreads();
-    Box<T, 3> bx;
+    constexpr int NST = ADAPT ? 4 : 3;
+    Box<T, NST> bx;
     bx.u = U;
     bx.st[0] = A.rc_sk + d.skoff;
     bx.st[1] = A.uk_sk + d.skoff;
     bx.st[2] = A.cold_sk + d.skoff;
+    if (ADAPT) bx.st[NST - 1] = A.theta_sk + d.skoff;
     bx.sb = A.mask_sk + d.skoff;
     bx.nx = d.mx;
     bx.ny = d.my;
     bx.nb = d.nb;
     bx.nstepp = d.nstepp;
-    Alg5Policy<T> pol{Hs, A.theta};
+    Alg5Policy<T> pol{Hs, A.theta, ADAPT};
     long long sweeps;
     bool conv;
-    engine_run<T, 3, true>(bx, pol, A.max_coarse, smem, sweeps, conv, &A.st->err);
+    engine_run<T, NST, true>(bx, pol, A.max_coarse, smem, sweeps, conv, &A.st->err);
     if (threadIdx.x == 0) {
         atomicMax(&A.st->coarse_sweeps_max, (unsigned long long)sweeps);
         if (!conv) atomicAdd(&A.st->coarse_caps, 1ull);
         atomicAdd(&A.st->coarse_updates, (unsigned long long)sweeps * d.mx * d.my);
     }
+}
+
+template <class T>
+__device__ __forceinline__ void k_step4_body(const DDArgs<T> &A, char *smem, int gidx) {
+    k_step4_gen<T, false>(A, smem, gidx);
+}
+template <class T>
+__device__ __forceinline__ void k_step4a_body(const DDArgs<T> &A, char *smem, int gidx) {
+    k_step4_gen<T, true>(A, smem, gidx);
 }
 
 // --------------------------------------------------------------------------
@@ -583,8 +601,28 @@ __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int 
 // --------------------------------------------------------------------------
 // Alg. 4 + inputs of Alg. 5
 // --------------------------------------------------------------------------
+// Per-node weight of Sec. 4.2 from du = u^k - u^{k-1} and the last n changes
+// dC[s] of C_H(nbrs U): eq. secthetaest (weighted mean of the changes), the
+// damping of eq. thetaest, the optional cap; `fallback` where undefined.
 template <class T>
-__device__ void alg4_body(const DDArgs<T> &A, size_t bid, size_t nbid) {
+__device__ inline double theta_estimate(const DDArgs<T> &A, double du, const double *dC, int n, double fallback) {
+    double den = 0.0, wsum = 0.0;
+    for (int s = 0; s < n; ++s) {
+        den = __dadd_rn(den, __dmul_rn(A.om[s], dC[s]));
+        wsum = __dadd_rn(wsum, A.om[s]);
+    }
+    if (!(wsum > 0.0)) return fallback;
+    den = __ddiv_rn(den, wsum);
+    const double t = __ddiv_rn(du, den);
+    if (!isfinite(t) || den == 0.0) return fallback;
+    const double sig = __ddiv_rn(1.0, __dadd_rn(1.0, exp(__ddiv_rn(__dsub_rn(t, A.sx0), A.sg))));
+    double v = __dadd_rn(__dmul_rn(sig, t), __dmul_rn(__dmul_rn(__dsub_rn(1.0, sig), A.sd), t));
+    if (A.cap > 0.0 && v > A.cap) v = A.cap;
+    return v > 0.0 ? v : 0.0;
+}
+
+template <class T>
+__device__ void alg4_body(const DDArgs<T> &A, int k, size_t bid, size_t nbid) {
     if (*A.done) return;
     const DDGeom &G = A.G;
     for (size_t a = bid * blockDim.x + threadIdx.x; a < G.coarse_elems; a += nbid * blockDim.x) {
@@ -633,6 +671,7 @@ __device__ void alg4_body(const DDArgs<T> &A, size_t bid, size_t nbid) {
         }
         const T ukv = A.cu[(size_t)best * G.coarse_elems + a];
         const uint8_t wkv = A.cw[(size_t)best * G.coarse_elems + a];
+        const T uold = A.uk[a];  // u^{k-1} (meaningful for k >= 1)
         A.uk[a] = ukv;
         A.wk[a] = wkv;
         A.u_out[(size_t)Y * A.sy + X] = ukv;
@@ -659,18 +698,34 @@ __device__ void alg4_body(const DDArgs<T> &A, size_t bid, size_t nbid) {
         const T cold = local_solve2_value(vmx, vpx, vmy, vpy, Num<T>::mul(rv > T(0) ? rv : T(0), T(G.H)));
         A.Uprev[a] = A.U[a];
         A.W[a] = wkv;
+        T th = A.theta;
+        if (A.adaptive) {
+            double thv = (double)A.theta;
+            if (k >= 1) {
+                const int n = k < 3 ? k : 3;
+                const T *c1 = A.Ch[(k + 3) & 3], *c2 = A.Ch[(k + 2) & 3], *c3 = A.Ch[(k + 1) & 3];
+                double dC[3] = {0.0, 0.0, 0.0};
+                dC[0] = __dsub_rn((double)cold, (double)c1[a]);
+                if (n > 1) dC[1] = __dsub_rn((double)c1[a], (double)c2[a]);
+                if (n > 2) dC[2] = __dsub_rn((double)c2[a], (double)c3[a]);
+                thv = theta_estimate(A, __dsub_rn((double)ukv, (double)uold), dC, n, (double)A.theta);
+            }
+            A.Ch[k & 3][a] = cold;
+            th = (T)thv;
+        }
         for (int dd = 0; dd < 4; ++dd) {
             size_t si = d.skoff + skew_index(dd, i, j, d.nb, d.my, d.nstepp);
             A.uk_sk[si] = ukv;
             A.mask_sk[si] = m;
             A.cold_sk[si] = cold;
+            if (A.adaptive) A.theta_sk[si] = th;
         }
     }
 }
 
 template <class T>
-__global__ void k_alg4(DDArgs<T> A) {
-    alg4_body(A, blockIdx.x, gridDim.x);
+__global__ void k_alg4(DDArgs<T> A, int k) {
+    alg4_body(A, k, blockIdx.x, gridDim.x);
 }
 
 template <class T>

@@ -14,6 +14,7 @@ struct DDPlan {
     size_t bytes;
     size_t fine_smem, step1_smem, step4_smem;
     int grid_threads;
+    bool adaptive;  // per-node weight: history of C_H and a fourth Alg. 5 static
 };
 
 // Checks a DD request (2-D or 3-D); sets the error text and returns false if
@@ -45,7 +46,15 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
     int *chg = cv.take<int>(4);
     unsigned *bar = cv.take<unsigned>(4);
     DevStats *st = cv.take<DevStats>(1);
+    T *Ch[4] = {nullptr, nullptr, nullptr, nullptr};
+    T *theta_sk = nullptr;
+    if (P.adaptive) {
+        for (int s = 0; s < 4; ++s) Ch[s] = cv.take<T>(G.coarse_elems);
+        theta_sk = cv.take<T>(G.coarse_sk_elems);
+    }
     if (A) {
+        for (int s = 0; s < 4; ++s) A->Ch[s] = Ch[s];
+        A->theta_sk = theta_sk;
         A->tile_state = tile_state;
         A->tile_rsk = tile_rsk;
         A->U = U;
@@ -111,6 +120,7 @@ inline DDPlan dd_plan(const eik_grid *grid, const eik_dd_params *p) {
     DDPlan P;
     P.G = make_geom((int)grid->n[0], (int)grid->n[1], p->tiles[0], p->tiles[1], p->coarse_ratio, grid->h);
     P.step1_smem = P.step4_smem = 0;
+    P.adaptive = p->theta_adaptive != 0;
     P.bytes = grid->dtype == EIK_F64 ? dd_layout<double>(P, nullptr, nullptr, p->max_iter)
                                      : dd_layout<float>(P, nullptr, nullptr, p->max_iter);
     const int gnb = ceil32(P.G.ncx + 1);
@@ -118,11 +128,13 @@ inline DDPlan dd_plan(const eik_grid *grid, const eik_dd_params *p) {
     if (grid->dtype == EIK_F64) {
         P.fine_smem = engine_smem_bytes<double, 1, false>(P.G.tnb, P.G.tny);
         P.step1_smem = engine_smem_bytes<double, 1, false>(gnb, P.G.ncy + 1);
-        P.step4_smem = engine_smem_bytes<double, 3, true>(gnb, P.G.ncy + 1);
+        P.step4_smem = P.adaptive ? engine_smem_bytes<double, 4, true>(gnb, P.G.ncy + 1)
+                                  : engine_smem_bytes<double, 3, true>(gnb, P.G.ncy + 1);
     } else {
         P.fine_smem = engine_smem_bytes<float, 1, false>(P.G.tnb, P.G.tny);
         P.step1_smem = engine_smem_bytes<float, 1, false>(gnb, P.G.ncy + 1);
-        P.step4_smem = engine_smem_bytes<float, 3, true>(gnb, P.G.ncy + 1);
+        P.step4_smem = P.adaptive ? engine_smem_bytes<float, 4, true>(gnb, P.G.ncy + 1)
+                                  : engine_smem_bytes<float, 3, true>(gnb, P.G.ncy + 1);
     }
     return P;
 }

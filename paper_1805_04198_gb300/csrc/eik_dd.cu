@@ -43,17 +43,20 @@ namespace eik {
     }
 EIK_KERNEL_PAIR(k_step1, 96, 224)
 EIK_KERNEL_PAIR(k_step4, 160, 224)
+EIK_KERNEL_PAIR(k_step4a, 160, 224)
 EIK_KERNEL_PAIR(k_fine, 96, 224)
 
 template <class T> struct DDKernels;
 template <> struct DDKernels<float> {
     static constexpr void (*step1)(DDArgs<float>) = k_step1_f32;
     static constexpr void (*step4)(DDArgs<float>) = k_step4_f32;
+    static constexpr void (*step4a)(DDArgs<float>) = k_step4a_f32;
     static constexpr void (*fine)(DDArgs<float>) = k_fine_f32;
 };
 template <> struct DDKernels<double> {
     static constexpr void (*step1)(DDArgs<double>) = k_step1_f64;
     static constexpr void (*step4)(DDArgs<double>) = k_step4_f64;
+    static constexpr void (*step4a)(DDArgs<double>) = k_step4a_f64;
     static constexpr void (*fine)(DDArgs<double>) = k_fine_f64;
 };
 
@@ -73,6 +76,10 @@ bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
     }
     if (grid && grid->ndim == 3) {
         if (!valid_grid_common(grid, 3)) return false;
+        if (p->theta_adaptive) {
+            set_error("the per-node weight (theta_adaptive) is implemented for 2-D grids");
+            return false;
+        }
         if (p->max_iter < 0 || p->max_iter > 100000 || p->max_fsm_sweeps < 1 || p->max_coarse_sweeps < 1 ||
             p->max_fsm_sweeps > MAX_SWEEPS || p->max_coarse_sweeps > MAX_SWEEPS || !std::isfinite(p->theta)) {
             set_error("max_iter must be in [0, 100000], sweep caps in [1, %lld], theta finite", MAX_SWEEPS);
@@ -116,6 +123,17 @@ bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
         set_error("theta must be finite");
         return false;
     }
+    if (p->theta_adaptive) {
+        const double w = p->omega[0] + p->omega[1] + p->omega[2];
+        bool ok = std::isfinite(p->sig_delta) && std::isfinite(p->sig_x0) && std::isfinite(p->theta_cap) &&
+                  p->sig_gamma > 0.0 && std::isfinite(p->sig_gamma) && w > 0.0 && std::isfinite(w);
+        for (int s2 = 0; s2 < 3; ++s2) ok = ok && p->omega[s2] >= 0.0;
+        if (!ok) {
+            set_error("adaptive theta: omega must be >= 0 with a positive finite sum, sig_gamma > 0, "
+                      "sig_delta, sig_x0 and theta_cap finite");
+            return false;
+        }
+    }
     return true;
 }
 
@@ -137,6 +155,12 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     A.max_iter = p->max_iter;
     A.max_fsm = p->max_fsm_sweeps;
     A.max_coarse = p->max_coarse_sweeps;
+    A.adaptive = P.adaptive ? 1 : 0;
+    for (int s2 = 0; s2 < 3; ++s2) A.om[s2] = p->omega[s2];
+    A.sg = p->sig_gamma;
+    A.sd = p->sig_delta;
+    A.sx0 = p->sig_x0;
+    A.cap = p->theta_cap;
     const DDGeom &G = P.G;
     const int ntiles = G.tx * G.ty;
 
@@ -158,7 +182,8 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.step1_smem),
                          "smem attr step1")))
         return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::step4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.step4_smem),
+    auto step4k = P.adaptive ? DDKernels<T>::step4a : DDKernels<T>::step4;
+    if ((rc = cuda_check(cudaFuncSetAttribute(step4k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.step4_smem),
                          "smem attr step4")))
         return rc;
     // causal sweep: cooperative grid sized to what is co-resident
@@ -189,10 +214,10 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     if ((rc = launch_causal(0))) return rc;
     for (int k = 0; k <= p->max_iter; ++k) {
         EIK_LAUNCH("dd_fine_subdomains", s, DDKernels<T>::fine<<<ntiles, 32 * G.tnb, P.fine_smem, s>>>(A)); ++nl;
-        EIK_LAUNCH("dd_alg4_restrict", s, k_alg4<T><<<eb, ew, 0, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd_alg4_restrict", s, k_alg4<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
         EIK_LAUNCH("dd_check", s, k_check<T><<<1, 1, 0, s>>>(A, k)); ++nl;
         if (k == p->max_iter) break;
-        EIK_LAUNCH("dd_step4_weighted", s, DDKernels<T>::step4<<<G.ngrids, P.grid_threads, P.step4_smem, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd_step4_weighted", s, step4k<<<G.ngrids, P.grid_threads, P.step4_smem, s>>>(A)); ++nl;
         if ((rc = launch_causal(1))) return rc;
         EIK_LAUNCH("dd_delta", s, k_delta<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
     }

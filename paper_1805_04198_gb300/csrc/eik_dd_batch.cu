@@ -149,11 +149,11 @@ __global__ void kb_pack(const DDArgs<T> *__restrict__ args, Segs tiles, Segs coa
 }
 
 template <class T>
-__global__ void kb_alg4(const DDArgs<T> *__restrict__ args, Segs S) {
+__global__ void kb_alg4(const DDArgs<T> *__restrict__ args, Segs S, int k) {
     for (int b = blockIdx.x; b < S.total; b += gridDim.x) {
         int local;
         const int p = seg_find(S.pre, S.n, b, local);
-        alg4_body(args[p], local, __ldg(S.pre + p + 1) - __ldg(S.pre + p));
+        alg4_body(args[p], k, local, __ldg(S.pre + p + 1) - __ldg(S.pre + p));
     }
 }
 
@@ -309,6 +309,10 @@ static bool batch_validate(int nprob, const eik_grid *grids, const eik_dd_params
         }
         if (grids[p].dtype != grids[0].dtype) {
             set_error("problem %d: every problem of a batch must have the same dtype", p);
+            return false;
+        }
+        if (params[p].theta_adaptive) {
+            set_error("problem %d: the batched solve takes a constant theta (theta_adaptive = 0)", p);
             return false;
         }
         if (!dd_validate(&grids[p], &params[p])) {
@@ -554,7 +558,7 @@ static int batch_run(int nprob, const eik_grid *grids, const void *const *r, con
                        BatchKernels<T>::fine<<<ctas(BatchKernels<T>::fine, c, fq), 32 * c.nw, c.smem, s>>>(dargs, item_list(c, fq)));
             ++nl;
         }
-        EIK_LAUNCH("dd_alg4_restrict", s, kb_alg4<T><<<eb, ELEM_BLOCK, 0, s>>>(dargs, coarse)); ++nl;
+        EIK_LAUNCH("dd_alg4_restrict", s, kb_alg4<T><<<eb, ELEM_BLOCK, 0, s>>>(dargs, coarse, k)); ++nl;
         EIK_LAUNCH("dd_check", s, kb_check<T><<<(nprob + 127) / 128, 128, 0, s>>>(dargs, nprob, k)); ++nl;
         if (k == B.max_iter) break;
         for (const BoxClass &c : B.grid) {

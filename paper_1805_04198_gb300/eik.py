@@ -49,7 +49,9 @@ class FsmStats(ctypes.Structure):
 class DDParams(ctypes.Structure):
     _fields_ = [("tiles", ctypes.c_int * 3), ("coarse_ratio", ctypes.c_int), ("theta", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("max_fsm_sweeps", ctypes.c_int64),
-                ("max_coarse_sweeps", ctypes.c_int64)]
+                ("max_coarse_sweeps", ctypes.c_int64), ("theta_adaptive", ctypes.c_int),
+                ("omega", ctypes.c_double * 3), ("sig_gamma", ctypes.c_double), ("sig_delta", ctypes.c_double),
+                ("sig_x0", ctypes.c_double), ("theta_cap", ctypes.c_double)]
 
 
 class DDStats(ctypes.Structure):
@@ -241,10 +243,13 @@ NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def dd_params(tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
-              max_coarse_sweeps=8) -> DDParams:
+              max_coarse_sweeps=8, theta_adaptive=False, omega=(1.0, 1.0, 1.0), sig_gamma=0.75, sig_delta=0.01,
+              sig_x0=0.9, theta_cap=0.0) -> DDParams:
     t = list(tiles) + [1] * (3 - len(tiles))
     return DDParams((ctypes.c_int * 3)(*t), int(coarse_ratio), float(theta), int(max_iter), float(tol),
-                    int(max_fsm_sweeps), int(max_coarse_sweeps))
+                    int(max_fsm_sweeps), int(max_coarse_sweeps), 1 if theta_adaptive else 0,
+                    (ctypes.c_double * 3)(*omega), float(sig_gamma), float(sig_delta), float(sig_x0),
+                    float(theta_cap))
 
 
 def fsm(r, gamma, g, h, max_sweeps=100000, stream=None, sync=True):
@@ -269,13 +274,15 @@ def fsm(r, gamma, g, h, max_sweeps=100000, stream=None, sync=True):
 
 
 def dd_solve(r, gamma, g, h, tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
-             max_coarse_sweeps=8, stream=None, sync=True):
-    """Two-scale DD solve (Sec. 3.2).  Returns (u, stats dict)."""
+             max_coarse_sweeps=8, stream=None, sync=True, **adaptive):
+    """Two-scale DD solve (Sec. 3.2).  Returns (u, stats dict).  Keyword
+    arguments theta_adaptive, omega, sig_gamma, sig_delta, sig_x0, theta_cap
+    select the per-node weight of Sec. 4.2 (see dd_params)."""
     _check_like(r, g)
     if gamma.dtype != torch.uint8 or gamma.shape != r.shape:
         raise ValueError("gamma must be uint8 with r's shape")
     grid = make_grid(r, h)
-    p = dd_params(tiles, coarse_ratio, theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps)
+    p = dd_params(tiles, coarse_ratio, theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps, **adaptive)
     nbytes = eik_dd_workspace_size(grid, p)
     if nbytes == 0:
         raise EikError(-1, eik_last_error())

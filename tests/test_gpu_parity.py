@@ -176,6 +176,41 @@ def test_fsm_full_size_fp32_against_oracle(gpu):
     assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
 
 
+@pytest.mark.parametrize("n,tiles,c,kmax", [
+    (65, (4, 4), 8, 6),
+    (97, (3, 3), 16, 5),
+    (129, (2, 2), 8, 4),
+])
+def test_dd_adaptive_theta_fp64_against_oracle(gpu, n, tiles, c, kmax):
+    """Per-node weight of Sec. 4.2: the first weighted update uses the constant
+    theta (bitwise); later ones use the estimate, which contains an exp whose
+    last bit may differ between the device and the host library, hence the
+    FP64 tolerance of 1e-11 relative."""
+    r, gamma, g, h = _dd_case(n, tiles, c)
+    kw = dict(theta=0.2, max_coarse_sweeps=8, theta_adaptive=True, theta_cap=1.0)
+    for k in range(1, kmax + 1):
+        u_ref, s_ref, _ = O.dd(r, gamma, g, h, tiles, c, max_iter=k, tol=0.0, **kw)
+        u, st = gpu.dd_solve(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h, tiles, c,
+                             max_iter=k, tol=0.0, **kw)
+        assert st["iters"] == s_ref["iters"] == k
+        a = u.cpu().numpy()
+        if k == 1:
+            np.testing.assert_array_equal(a, u_ref)
+        else:
+            assert _rel(a, u_ref) <= 1e-11, k
+
+
+def test_dd_adaptive_theta_validation(gpu):
+    r = torch.ones((65, 65), dtype=torch.float64, device=DEV)
+    G = torch.zeros((65, 65), dtype=torch.uint8, device=DEV)
+    with pytest.raises(gpu.EikError):
+        gpu.dd_solve(r, G, r, 1.0 / 64, (4, 4), 8, theta_adaptive=True, sig_gamma=0.0)
+    r3 = torch.ones((17, 17, 17), device=DEV)
+    G3 = torch.zeros((17, 17, 17), dtype=torch.uint8, device=DEV)
+    with pytest.raises(gpu.EikError):
+        gpu.dd_solve(r3, G3, r3, 1.0 / 16, (2, 2, 2), 4, theta_adaptive=True)
+
+
 # The DD workload of the benchmark: 4097^2, 16x16 subdomains, coarse ratio 16,
 # theta 0.2, FP32, in the launch configuration bench.py times.
 C1_DD = dict(theta=0.2, tol=1e-6, max_coarse_sweeps=8)
