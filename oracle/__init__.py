@@ -13,6 +13,8 @@ Functions (each follows the paper section named in its docstring):
   adjoint      discrete adjoint of the converged Godunov system (no paper
                counterpart; checked by finite differences)
   theta_estimate  per-node weight of Sec. 4.2 (eqs. secthetaest, thetaest)
+  model_problem   Sec. 4's model problem, eq. modelprob, with the bounds of
+               Theorem 2's proof
 """
 from __future__ import annotations
 
@@ -211,3 +213,95 @@ def adjoint(r, gamma, u, dJdu, h):
     out = np.zeros_like(r)
     lib.orc_adjoint(d, n, float(h), _dp(r), _bp(gamma), _dp(u), _dp(dJdu), _dp(out))
     return out
+
+
+def model_problem(N, M, theta, max_iter):
+    """The model problem of Sec. 4 and its weighted iteration, eq. modelprob.
+
+    Strip [0, 1] x [0, H], H = 1/N, r = 1, Gamma = the bottom edge and the
+    left edge with g = sqrt(x^2 + y^2); fine step h = H/M, coarse nodes
+    X_ij = (iH, jh), i = 0..N, j = 0..M.  The coarse solver is the one printed
+    with eq. modelprob: U_{i-1,j} + H for j < M, the two-term Godunov formula
+    in U_{i-1,M} and U_{i,0} for j = M (min + H where the two differ by H or
+    more, the causality branch of Sec. 3.2's C_H).  u^k_{.,i} is the fine FSM
+    solution of subdomain [(i-1)H, iH] x [0, H] with Dirichlet data U^k on its
+    left column and g on its bottom row, read at x = iH; u^f is the FSM
+    solution of the whole strip.  U^0 = C_H(U^0) (eq. modelprob's initial
+    condition), the left column and bottom row of U stay at u^f (eqs. modelBC1,
+    modelBC2), and for k >= 0, i = 1..N in order:
+        U^{k+1}_ij = theta^{k+1}_ij [C_H(U^{k+1}_{i-1,j}) - C_H(U^k_{i-1,j})] + u^k_ij.
+
+    ``theta`` is a constant or a callable theta(k1, i, j, mbar, Mbar) giving
+    theta^{k1}_ij from the bounds of Theorem 2's proof,
+        mbar = (U^k_ij - u^k_ij) / D,  Mbar = (u^f_ij - u^k_ij) / D,
+        D = C_H(U^{k+1}_{i-1,j}) - C_H(U^k_{i-1,j})   (NaN where D = 0).
+
+    Returns dict with arrays indexed [k][j, i]: U (k = 0..max_iter), u
+    (k = 0..max_iter-1), mbar and Mbar (k = 1..max_iter at list index k-1),
+    and uf [j, i].
+    """
+    H = 1.0 / N
+    h = H / M
+    nx = N * M + 1
+
+    def g_at(l, m):
+        return float(np.hypot(l * h, m * h))
+
+    def strip(ncol, x0, left):
+        r = np.ones((M + 1, ncol + 1))
+        gam = np.zeros((M + 1, ncol + 1), np.uint8)
+        gv = np.zeros((M + 1, ncol + 1))
+        gam[:, 0] = 1
+        gv[:, 0] = left
+        gam[0, :] = 1
+        gv[0, :] = [g_at(x0 + l, 0) for l in range(ncol + 1)]
+        u, _, _ = fsm(r, gam, gv, h)
+        return u
+
+    ufull = strip(nx - 1, 0, [g_at(0, m) for m in range(M + 1)])
+    uf = np.ascontiguousarray(ufull[:, ::M])
+
+    def CH(a, i, j):
+        if j < M:
+            return a + H
+        b = uf[0, i]
+        if abs(a - b) >= H:
+            return min(a, b) + H
+        return 0.5 * (a + b + np.sqrt(2.0 * H * H - (a - b) ** 2))
+
+    def fine(U):
+        u = np.empty_like(U)
+        u[:, 0] = U[:, 0]
+        for i in range(1, N + 1):
+            u[:, i] = strip(M, (i - 1) * M, U[:, i - 1])[:, M]
+        u[0, :] = uf[0, :]
+        return u
+
+    U0 = np.empty((M + 1, N + 1))
+    U0[:, 0] = uf[:, 0]
+    U0[0, :] = uf[0, :]
+    for i in range(1, N + 1):
+        for j in range(1, M + 1):
+            U0[j, i] = CH(U0[j, i - 1], i, j)
+    Us, us, mb, Mb = [U0], [], [], []
+    for k in range(max_iter):
+        Uk = Us[-1]
+        uk = fine(Uk)
+        Un = np.empty_like(Uk)
+        Un[:, 0] = uf[:, 0]
+        Un[0, :] = uf[0, :]
+        mk = np.full_like(Uk, np.nan)
+        Mk = np.full_like(Uk, np.nan)
+        for i in range(1, N + 1):
+            for j in range(1, M + 1):
+                D = CH(Un[j, i - 1], i, j) - CH(Uk[j, i - 1], i, j)
+                if D != 0.0:
+                    mk[j, i] = (Uk[j, i] - uk[j, i]) / D
+                    Mk[j, i] = (uf[j, i] - uk[j, i]) / D
+                t = theta(k + 1, i, j, mk[j, i], Mk[j, i]) if callable(theta) else theta
+                Un[j, i] = t * D + uk[j, i]
+        us.append(uk)
+        mb.append(mk)
+        Mb.append(Mk)
+        Us.append(Un)
+    return {"U": Us, "u": us, "mbar": mb, "Mbar": Mb, "uf": uf}

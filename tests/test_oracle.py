@@ -340,3 +340,67 @@ def test_dd_adaptive_theta_first_update_and_theorem1():
                           theta_adaptive=True, theta_cap=1.0)
         for i in range(k + 1):
             assert np.array_equal(U[1:, i * M], uf[1:, i * M]), (k, i)
+
+
+def _mp_mid(k1, i, j, mb, Mb):
+    """A weight inside Theorem 2's interval (max(mbar, 0), Mbar)."""
+    if not np.isfinite(Mb):
+        return 0.0
+    return 0.5 * (max(mb, 0.0) + Mb)
+
+
+def test_model_problem_theorem1():
+    """Theorem 1 (Sec. 4.1) on the model problem's own iteration, eq.
+    modelprob: U^k = u^f on every column i <= k, bitwise, whatever the
+    weights (constant 0.2, 1, or chosen per node)."""
+    N, M = 10, 8
+    for th in (0.2, 1.0, _mp_mid):
+        R = O.model_problem(N, M, th, N)
+        for k in range(N + 1):
+            assert np.array_equal(R["U"][k][:, :k + 1], R["uf"][:, :k + 1]), (th, k)
+        assert not np.array_equal(R["U"][1][:, 2:], R["uf"][:, 2:])
+
+
+def test_model_problem_theorem2():
+    """Theorem 2 (Sec. 4.1) at the paper's sizes H = 1/20, h = 1/1000: with
+    every weight inside (max(mbar, 0), Mbar) the iterates decrease strictly
+    and stay strictly above u^f on the columns i > k; the interval is never
+    empty there and Mbar > 0.  Taking the weight Mbar itself puts the node on
+    u^f, and a weight above it below u^f (the bound is sharp)."""
+    N, M = 20, 50
+    R = O.model_problem(N, M, _mp_mid, 5)
+    uf = R["uf"]
+    for k in range(1, 6):
+        U, Up = R["U"][k], R["U"][k - 1]
+        mb, Mb = R["mbar"][k - 1][1:, k + 1:], R["Mbar"][k - 1][1:, k + 1:]
+        assert np.all(Mb > 0) and np.all(Mb > np.maximum(mb, 0.0)), k
+        assert np.all(U[1:, k + 1:] < Up[1:, k + 1:]), k
+        assert np.all(U[1:, k + 1:] > uf[1:, k + 1:]), k
+    col = 2   # the first column whose coarse-solver change does not depend on upstream weights
+
+    def at_bound(scale):
+        def f(k1, i, j, mb, Mb):
+            return scale * Mb if i == col else _mp_mid(k1, i, j, mb, Mb)
+        return f
+
+    U1 = O.model_problem(N, M, at_bound(1.0), 1)["U"][1]
+    np.testing.assert_allclose(U1[1:, col], uf[1:, col], rtol=1e-14, atol=0)
+    U1 = O.model_problem(N, M, at_bound(1.05), 1)["U"][1]
+    assert np.all(U1[1:, col] < uf[1:, col])
+
+
+def test_model_problem_theta_one_peaks():
+    """Sec. 4 (figure for theta = 1, H = 1/20, h = 1/1000): with theta = 1 the
+    error max|U^k - u^f| grows from the first iteration and peaks around
+    k = 10 before Theorem 1 brings it to zero at k = N; a small weight
+    (0.1) decreases it at every iteration."""
+    N, M = 20, 50
+    R = O.model_problem(N, M, 1.0, N)
+    e = [np.abs(U - R["uf"]).max() for U in R["U"]]
+    peak = int(np.argmax(e))
+    assert 8 <= peak <= 12, peak
+    assert all(e[k + 1] > e[k] for k in range(peak)), e
+    assert e[1] > 10 * e[0] and e[N] == 0.0
+    R = O.model_problem(N, M, 0.1, N)
+    e = [np.abs(U - R["uf"]).max() for U in R["U"]]
+    assert all(e[k + 1] <= e[k] for k in range(N)), e
