@@ -3,8 +3,11 @@
 Workload (default): 2-D 4097^2 grid (h = 1/4096), slowness r = clip(1 + 0.3x +
 0.4 F/max|F|, 0.2) with F a sum of 32 seeded Fourier modes, |k| in [64, 128]
 (eps = 1/64); Gamma = the whole left edge x = 0, g = 0; 16 x 16 subdomains,
-coarse ratio 16 (coarse grid 257^2); FP32 storage; theta = 0.2; stop when the
+coarse ratio 16 (coarse grid 257^2); FP32 storage; the per-node weight of
+Sec. 4.2 (omega = (1, 1, 1), sigmoid damping gamma 0.75, delta 0.01, x0 0.9,
+capped at 0.3; constant 0.2 where the estimate is undefined); stop when the
 coarse update falls below 1e-6 or after 2*16 + 10 = 42 iterations.
+--theta 0.2 runs the constant-weight iteration of Sec. 3.2 instead.
 
 One step = one complete eik_dd_solve (set-up, Step 1, all parareal iterations)
 on device-resident inputs.  value = local Godunov solves executed per second
@@ -40,7 +43,8 @@ METRIC = "time-to-solution & Gcell-updates/s vs plain GPU full-grid FSM at equal
 N_SIDE = 4097
 TILES = 16
 COARSE = 16
-THETA = 0.2
+THETA = 0.2          # constant weight, and the fallback of the adaptive weight
+THETA_CAP = 0.3      # cap on the adaptive weight (cap 1 diverges on this workload)
 MAX_ITER = 2 * TILES + 10
 TOL = 1e-6
 MAX_COARSE_SWEEPS = 8
@@ -189,6 +193,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--theta", default="adaptive",
+                    help="'adaptive' (per-node weight of Sec. 4.2, the default) or a constant weight")
     ap.add_argument("--workload", default="dd4097", choices=["dd4097", "batch256", "dd3d257", "tomography1025"],
                     help="dd4097 (default) is the benchmark line; the others measure the batched solve, the "
                          "3-D solve and the tomography gradient with the same keys")
@@ -221,6 +227,13 @@ def main():
     g = torch.from_numpy(g32).to(dev)
     tiles = (TILES, TILES)
     dd_kw = dict(theta=THETA, max_iter=MAX_ITER, tol=TOL, max_coarse_sweeps=MAX_COARSE_SWEEPS)
+    if args.theta == "adaptive":
+        dd_kw.update(theta_adaptive=True, theta_cap=THETA_CAP)
+        theta_cfg = {"rule": "adaptive, Sec. 4.2", "omega": [1.0, 1.0, 1.0], "sig_gamma": 0.75,
+                     "sig_delta": 0.01, "sig_x0": 0.9, "cap": THETA_CAP, "fallback": THETA}
+    else:
+        dd_kw["theta"] = float(args.theta)
+        theta_cfg = dd_kw["theta"]
 
     # buffers allocated once, outside the timed region
     grid = eik.make_grid(R, h)
@@ -369,7 +382,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "c1_2d_4097_leftedge_16x16_c16", "n": N_SIDE, "tiles": TILES,
-                       "coarse_ratio": COARSE, "theta": THETA, "max_iter": MAX_ITER, "tol": TOL,
+                       "coarse_ratio": COARSE, "theta": theta_cfg, "max_iter": MAX_ITER, "tol": TOL,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"},
             "time_to_solution_ms": ms_per_step,
             "gcells_per_s": cells * world / (ms_per_step / 1e3) / 1e9,

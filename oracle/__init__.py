@@ -224,8 +224,9 @@ def model_problem(N, M, theta, max_iter):
     with eq. modelprob: U_{i-1,j} + H for j < M, the two-term Godunov formula
     in U_{i-1,M} and U_{i,0} for j = M (min + H where the two differ by H or
     more, the causality branch of Sec. 3.2's C_H).  u^k_{.,i} is the fine FSM
-    solution of subdomain [(i-1)H, iH] x [0, H] with Dirichlet data U^k on its
-    left column and g on its bottom row, read at x = iH; u^f is the FSM
+    solution of subdomain [(i-1)H, iH] x [0, H] with U^k held fixed on its
+    left column (the form the proof of Theorem 1 uses: u^k is computed from
+    the values U^k) and g on its bottom row, read at x = iH; u^f is the FSM
     solution of the whole strip.  U^0 = C_H(U^0) (eq. modelprob's initial
     condition), the left column and bottom row of U stay at u^f (eqs. modelBC1,
     modelBC2), and for k >= 0, i = 1..N in order:

@@ -17,10 +17,12 @@
  *    state (path-independent; equal to the last stored wind except at exact
  *    neighbour ties);
  *  - an FSM (fine or coarse) stops after the first sweep that changes nothing;
- *  - Step 2: a boundary node is Dirichlet (fixed at U) when W.n > 0 for some
- *    inward normal n of the subdomain, otherwise free (starts at +inf and is
- *    updated with one-sided differences); Gamma is fixed at g in every grid;
- *    the wind of a Dirichlet node is W;
+ *  - Steps 2-3: a subdomain boundary node starts at U when W.n > 0 for some
+ *    inward normal n of the subdomain (inflow), otherwise at +inf; every
+ *    boundary node is then swept like an interior one, with one-sided
+ *    differences (Step 3), so an inflow value can only decrease; only Gamma
+ *    stays fixed (at g).  The wind of an inflow node whose value never moved
+ *    is W, otherwise that of its local solve;
  *  - Alg. 4 / Alg. 5 at a node lying on several coarse lines (or interfaces):
  *    the agreement test is applied per axis and must pass on every axis;
  *  - Alg. 5 keeps the paper's overwrite update, evaluated as
@@ -650,14 +652,16 @@ static long step23_tile(const geom_t *G, const int *t, double h, const double *r
                         const double *g, const double *U, const signed char *W, double *ut, signed char *wt,
                         long max_sweeps, long *caps)
 {
-    long m[3], M, x, y, z, s;
-    double *rl;
-    unsigned char *fl;
+    long m[3], M, x, y, z, s, l;
+    double *rl, *u0;
+    unsigned char *fl, *in;
     int conv, k;
     for (k = 0; k < 3; ++k) m[k] = (k < G->d) ? G->S[k] + 1 : 1;
     M = m[0] * m[1] * m[2];
     rl = malloc(sizeof(double) * (size_t)M);
+    u0 = malloc(sizeof(double) * (size_t)M);
     fl = malloc((size_t)M);
+    in = malloc((size_t)M);
     for (z = 0; z < m[2]; ++z)
         for (y = 0; y < m[1]; ++y)
             for (x = 0; x < m[0]; ++x) {
@@ -666,6 +670,7 @@ static long step23_tile(const geom_t *G, const int *t, double h, const double *r
                 for (k = 0; k < 3; ++k) xf[k] = (k < G->d) ? t[k] * G->S[k] + lc[k] : 0;
                 f = xf[0] + G->n[0] * (xf[1] + G->n[1] * xf[2]);
                 rl[l] = r[f];
+                in[l] = 0;
                 for (k = 0; k < 3; ++k) wt[3 * l + k] = 0;
                 if (gamma[f]) {
                     fl[l] = 1;
@@ -683,20 +688,29 @@ static long step23_tile(const geom_t *G, const int *t, double h, const double *r
                         if (W[3 * f + k] < 0) inflow = 1;
                     }
                 }
-                if (face && inflow) {
-                    fl[l] = 1;
-                    ut[l] = U[f];
-                    for (k = 0; k < 3; ++k) wt[3 * l + k] = W[3 * f + k];
-                } else {
-                    fl[l] = 0;
-                    ut[l] = INF;
-                }
+                fl[l] = 0;
+                ut[l] = (face && inflow) ? U[f] : INF;
+                in[l] = (unsigned char)(face && inflow);
             }
+    memcpy(u0, ut, sizeof(double) * (size_t)M);
     s = fsm_local(G->d, m, h, rl, fl, ut, max_sweeps, &conv);
     if (!conv) ++*caps;
     winds_local(G->d, m, h, rl, fl, ut, wt);
+    /* an inflow node that kept its boundary value keeps the coarse wind W */
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long xf[3], f, lc[3] = {x, y, z};
+                l = lidx(m, x, y, z);
+                if (!in[l] || ut[l] != u0[l]) continue;
+                for (k = 0; k < 3; ++k) xf[k] = (k < G->d) ? t[k] * G->S[k] + lc[k] : 0;
+                f = xf[0] + G->n[0] * (xf[1] + G->n[1] * xf[2]);
+                for (k = 0; k < 3; ++k) wt[3 * l + k] = W[3 * f + k];
+            }
     free(rl);
+    free(u0);
     free(fl);
+    free(in);
     return s;
 }
 

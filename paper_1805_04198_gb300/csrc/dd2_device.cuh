@@ -67,7 +67,7 @@ __device__ __forceinline__ T fine_at(const T *a, long long sy, int X, int Y) {
 // --------------------------------------------------------------------------
 
 // FSM update u = min(u, u~) (Sec. 1.1, eq. FSMupdate).  Statics: r, stored
-// as a non-positive value at fixed nodes (Gamma, Dirichlet boundary data).
+// as a non-positive value at fixed nodes (Gamma).
 template <class T>
 struct FsmPolicy {
     T h;
@@ -511,8 +511,8 @@ __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int 
     const int tx = tile % G.tx, ty = tile / G.tx;
     const int NX = G.tnx, NY = G.tny;
     T *ut = A.tile_state + (size_t)tile * G.tile_elems;
-    T *rsk = A.tile_rsk + (size_t)tile * G.tile_sk_elems;
-    // Step 2: boundary data.  Interior and outflow nodes start at +inf.
+    // Step 2: boundary data.  Inflow nodes start at U, interior and outflow
+    // nodes at +inf; all of them are swept (Step 3), only Gamma is fixed.
     for (size_t e = threadIdx.x; e < G.tile_elems; e += blockDim.x) {
         int b = (int)(e / ((size_t)NY * 32));
         int rem = (int)(e % ((size_t)NY * 32));
@@ -526,20 +526,8 @@ __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int 
         }
         ut[e] = v;
     }
-    // fixed-node marks of the face nodes for this iteration: Dirichlet (inflow)
-    // and Gamma nodes carry a non-positive slowness in the skewed statics
-    for (int f = threadIdx.x; f < 2 * NY + 2 * NX; f += blockDim.x) {
-        int xl, yl;
-        if (f < NY) { xl = 0; yl = f; }
-        else if (f < 2 * NY) { xl = NX - 1; yl = f - NY; }
-        else if (f < 2 * NY + NX) { xl = f - 2 * NY; yl = 0; }
-        else { xl = f - 2 * NY - NX; yl = NY - 1; }
-        int X = tx * G.sx + xl, Y = ty * G.sy + yl;
-        size_t ca;
-        const bool fixed = A.gamma[(size_t)Y * A.sy + X] || tile_inflow(A, xl, yl, X, Y, ca);
-        const T v = fixed ? T(-1) : fine_at(A.r, A.sy, X, Y);
-        for (int dd = 0; dd < 4; ++dd) rsk[skew_index(dd, xl, yl, G.tnb, NY, G.tnstepp)] = v;
-    }
+    // (Gamma nodes carry a non-positive slowness in the skewed statics, set
+    // once when the statics are packed)
     __threadfence_block();
     __syncthreads();
     // Step 3: FSM sweeps in the subdomain
@@ -578,8 +566,8 @@ __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int 
             w = WIND_ZERO;
         } else {
             size_t ca2;
-            if (tile_inflow(A, xl, yl, X, Y, ca2)) {
-                w = A.W[ca];
+            if (tile_inflow(A, xl, yl, X, Y, ca2) && uv == A.U[ca]) {
+                w = A.W[ca];  // inflow value kept: the coarse wind
             } else if (uv < INF) {
                 T vmx = xl > 0 ? __ldcg(ut + box_index(xl - 1, yl, NY)) : INF;
                 T vpx = xl + 1 < NX ? __ldcg(ut + box_index(xl + 1, yl, NY)) : INF;

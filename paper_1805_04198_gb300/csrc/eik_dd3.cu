@@ -217,7 +217,7 @@ __device__ void box3_sweeps(T *su, int mx, int my, int mz, const P &pol, long lo
 // FSM update (Sec. 1.1): u = min(u, u~) at free nodes.
 template <class T>
 struct Fsm3 {
-    const uint8_t *fixed;  // shared, per box node
+    const uint8_t *fixed;  // shared, per box node; 1 = fixed (Gamma), 2 = swept inflow node
     const T *r;            // per box node, via rix
     long long r0, rsx, rsy, rsz;  // global index of box node (x,y,z) = r0 + x*rsx + y*rsy + z*rsz
     T hs;
@@ -232,7 +232,7 @@ struct Fsm3 {
     __device__ __forceinline__ void fill(Stat &st, int idx) const { st.fixed = fixed[idx]; }
     __device__ __forceinline__ T apply(T self, const T *vm, const T *vp, const Stat &st, int,
                                        bool &changed) const {
-        if (st.fixed) return self;
+        if (st.fixed == 1) return self;
         uint8_t w;
         const T ut = local_solve3(vm, vp, Num<T>::mul(st.r, hs), w);
         changed = ut < self;
@@ -442,7 +442,8 @@ __global__ void __launch_bounds__(BOX3_THREADS, 1) k3_fine(DD3Args<T> A) {
     T *su = reinterpret_cast<T *>(smem);
     uint8_t *fx = reinterpret_cast<uint8_t *>(su + (size_t)mz * ps);
     const int b0 = t0 * G.S[0], b1 = t1 * G.S[1], b2 = t2 * G.S[2];
-    // Step 2: boundary data; interior and outflow nodes start at +inf
+    // Step 2: boundary data; inflow nodes start at U (and are swept like the
+    // rest), interior and outflow nodes at +inf; Gamma is fixed at g
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int l[3] = {e % mx, (e / mx) % my, e / (mx * my)};
         const int Xg[3] = {b0 + l[0], b1 + l[1], b2 + l[2]};
@@ -484,9 +485,9 @@ __global__ void __launch_bounds__(BOX3_THREADS, 1) k3_fine(DD3Args<T> A) {
         }
         const long long ca = coarse_addr3(A, Xg[0], Xg[1], Xg[2]);
         uint8_t w = WIND_ZERO;
-        if (fx[q] == 2) {
-            w = A.W[ca];
-        } else if (fx[q] == 0 && uv < INF) {
+        if (fx[q] == 2 && uv == A.U[ca]) {
+            w = A.W[ca];  // inflow value kept: the coarse wind
+        } else if (fx[q] != 1 && uv < INF) {
             T vm[3], vp[3];
             vm[0] = l[0] > 0 ? su[q - 1] : INF;
             vp[0] = l[0] + 1 < mx ? su[q + 1] : INF;

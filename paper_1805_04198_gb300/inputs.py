@@ -180,3 +180,68 @@ def workload_c4(n=1025, nsrc=64, nrec=256):
     rec_rows = [4 * m + 2 for m in range(nrec)]
     return dict(name="c4_2d_%d_tomography" % n, r_true=r_true, r0=r0, h=h, src_rows=src_rows,
                 rec_rows=rec_rows, n=n)
+
+
+# --------------------------------------------------------------------------
+# Obstacle and random workloads of Sec. 4 ("Mazes and obstacles",
+# "Multiscale slowness functions"), unit square, Gamma = one node.
+# --------------------------------------------------------------------------
+SEED_CHECKER = 1805041984
+
+
+def _box_mask(X, Y, x0, x1, y0, y1):
+    return (X >= x0 - 1e-12) & (X <= x1 + 1e-12) & (Y >= y0 - 1e-12) & (Y <= y1 + 1e-12)
+
+
+def workload_fast_strip(n=501, tiles=10):
+    """The fast obstacle r^4: r = 0.01 on [0.26, 0.27] x [0, 0.6], r = 1
+    elsewhere, source at (0, 0); H = 1/tiles (1/10) and h = 1/(n-1) (1/500),
+    coarse ratio = subdomain width (the paper's construction)."""
+    h = 1.0 / (n - 1)
+    x, y = node_coords((n, n), h)
+    X, Y = np.meshgrid(x, y)
+    r = np.ones((n, n))
+    r[_box_mask(X, Y, 0.26, 0.27, 0.0, 0.6)] = 0.01
+    gamma, g = point_source((n, n), (0, 0))
+    S = (n - 1) // tiles
+    return dict(name="fast_strip_%d" % n, r=r, gamma=gamma, g=g, h=h, tiles=(tiles, tiles), c=S)
+
+
+def workload_maze(n=501, tiles=10):
+    """Stand-in for the maze r^3, whose exact geometry is only drawn in a
+    figure: slow barriers (r = 1000) and a fast obstacle (r = 0.01) with the
+    features the text names, r = 1 elsewhere, source at (0, 0).
+      * a solid slow disc containing a whole subdomain: centre (0.55, 0.45),
+        radius 0.09 (contains [0.5, 0.6] x [0.4, 0.5]);
+      * a fast disc inside one subdomain: centre (0.25, 0.75), radius 0.03;
+      * a slow wall on the coarse line x = 0.4, y in [0, 0.7], 3 nodes thick
+        (coarse nodes inside the obstacle), and a slow wall y in [0.845,
+        0.855], x in [0.15, 1] (no coarse line inside it)."""
+    h = 1.0 / (n - 1)
+    x, y = node_coords((n, n), h)
+    X, Y = np.meshgrid(x, y)
+    r = np.ones((n, n))
+    r[(X - 0.55) ** 2 + (Y - 0.45) ** 2 <= 0.09 ** 2] = 1000.0
+    r[_box_mask(X, Y, 0.4 - h, 0.4 + h, 0.0, 0.7)] = 1000.0
+    r[_box_mask(X, Y, 0.15, 1.0, 0.845, 0.855)] = 1000.0
+    r[(X - 0.25) ** 2 + (Y - 0.75) ** 2 <= 0.03 ** 2] = 0.01
+    gamma, g = point_source((n, n), (0, 0))
+    S = (n - 1) // tiles
+    return dict(name="maze_standin_%d" % n, r=r, gamma=gamma, g=g, h=h, tiles=(tiles, tiles), c=S)
+
+
+def workload_checkerboard(n=1401, tiles=14, eps_nodes=7, seed=SEED_CHECKER):
+    """Random periodic checkerboard: squares of side eps = eps_nodes * h, each
+    independently slowness 1 or 2 with probability 1/2 (SplitMix64, one draw
+    per square in row-major order); source at the centre; H = 1/tiles (1/14),
+    h = 1/(n-1) (1/1400), coarse ratio = subdomain width."""
+    h = 1.0 / (n - 1)
+    m = (n + eps_nodes - 1) // eps_nodes
+    rng = SplitMix64(seed)
+    cells = np.array([1.0 + (rng.next_u64() >> 63) for _ in range(m * m)]).reshape(m, m)
+    idx = np.arange(n) // eps_nodes
+    r = cells[np.ix_(idx, idx)]
+    gamma, g = point_source((n, n), ((n - 1) // 2, (n - 1) // 2))
+    S = (n - 1) // tiles
+    return dict(name="checkerboard_%d_eps%dh" % (n, eps_nodes), r=r, gamma=gamma, g=g, h=h,
+                tiles=(tiles, tiles), c=S)

@@ -96,6 +96,30 @@ def test_dd_fp64_bitwise(gpu, n, tiles, c, theta, kmax):
         np.testing.assert_array_equal(u.cpu().numpy(), u_ref, err_msg="k=%d" % k)
 
 
+@pytest.mark.parametrize("name,kw,ks", [
+    ("fast_strip", dict(n=101), (0, 4, 12, 30)),
+    ("maze", dict(n=201), (0, 4, 12, 30)),
+    ("checkerboard", dict(n=141, tiles=7), (0, 4, 12, 30)),
+    ("fast_strip", dict(n=501), (30,)),        # the paper's sizes, H = 1/10, h = 1/500
+])
+def test_dd_obstacles_fp64_bitwise(gpu, name, kw, ks):
+    """Sec. 4 obstacle and random workloads (subdomain boundary values that
+    the subdomain solve must lower): bitwise equal to the oracle, and at 30
+    iterations on the fine solution u^f within 1e-8 (with the 8-sweep cap on
+    Step 4 the fast strip settles 1.4e-9 away from u^f)."""
+    w = getattr(I, "workload_" + name)(**kw)
+    args = (_t(w["r"], torch.float64), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float64), w["h"],
+            w["tiles"], w["c"])
+    for k in ks:
+        u_ref, s_ref, _ = O.dd(w["r"], w["gamma"], w["g"], w["h"], w["tiles"], w["c"], theta=0.2, max_iter=k,
+                               tol=0.0, max_coarse_sweeps=8)
+        u, st = gpu.dd_solve(*args, theta=0.2, max_iter=k, tol=0.0, max_coarse_sweeps=8)
+        assert st["iters"] == s_ref["iters"] == k
+        np.testing.assert_array_equal(u.cpu().numpy(), u_ref, err_msg="%s k=%d" % (name, k))
+    uf, _, _ = O.fsm(w["r"], w["gamma"], w["g"], w["h"])
+    assert _rel(u.cpu().numpy(), uf) < 1e-8
+
+
 def test_dd_fp64_tol_stop_and_stats(gpu):
     r, gamma, g, h = _dd_case(65, (4, 4), 8, amp=0.3)
     u_ref, s_ref, log = O.dd(r, gamma, g, h, (4, 4), 8, theta=0.2, max_iter=40, tol=1e-9, max_coarse_sweeps=8)
