@@ -25,6 +25,10 @@
  *    is W, otherwise that of its local solve;
  *  - Alg. 4 / Alg. 5 at a node lying on several coarse lines (or interfaces):
  *    the agreement test is applied per axis and must pass on every axis;
+ *  - Alg. 4's minimum is taken over the fine solutions: a copy from a
+ *    subdomain for which the node was inflow and whose solve kept the Step 2
+ *    value U (an echo of the boundary data, not a solution) is not a
+ *    candidate unless every copy is one;
  *  - Alg. 5 keeps the paper's overwrite update, evaluated as
  *    u^k + theta (U~ - C_H(U^k)); when U~ or C_H(U^k) is +inf it takes u^k;
  *  - causal sweep (Alg. 2): repeated until nothing changes (its least fixed
@@ -650,7 +654,7 @@ static long step4_grid(const geom_t *G, const long *o, double H, double theta, c
  * ut/wt: the subdomain's local arrays ((S+1)^d nodes). */
 static long step23_tile(const geom_t *G, const int *t, double h, const double *r, const unsigned char *gamma,
                         const double *g, const double *U, const signed char *W, double *ut, signed char *wt,
-                        long max_sweeps, long *caps)
+                        unsigned char *echo, long max_sweeps, long *caps)
 {
     long m[3], M, x, y, z, s, l;
     double *rl, *u0;
@@ -696,13 +700,15 @@ static long step23_tile(const geom_t *G, const int *t, double h, const double *r
     s = fsm_local(G->d, m, h, rl, fl, ut, max_sweeps, &conv);
     if (!conv) ++*caps;
     winds_local(G->d, m, h, rl, fl, ut, wt);
-    /* an inflow node that kept its boundary value keeps the coarse wind W */
+    /* an inflow node that kept its boundary value keeps the coarse wind W and
+     * is marked as an echo of the boundary data (Alg. 4 reads the mark) */
     for (z = 0; z < m[2]; ++z)
         for (y = 0; y < m[1]; ++y)
             for (x = 0; x < m[0]; ++x) {
                 long xf[3], f, lc[3] = {x, y, z};
                 l = lidx(m, x, y, z);
-                if (!in[l] || ut[l] != u0[l]) continue;
+                echo[l] = (unsigned char)(in[l] && ut[l] == u0[l]);
+                if (!echo[l]) continue;
                 for (k = 0; k < 3; ++k) xf[k] = (k < G->d) ? t[k] * G->S[k] + lc[k] : 0;
                 f = xf[0] + G->n[0] * (xf[1] + G->n[1] * xf[2]);
                 for (k = 0; k < 3; ++k) wt[3 * l + k] = W[3 * f + k];
@@ -715,7 +721,8 @@ static long step23_tile(const geom_t *G, const int *t, double h, const double *r
 }
 
 /* Alg. 4 at every coarse-set node: choose u^k, w^k among the subdomain copies. */
-static void alg4(const geom_t *G, double **tu, signed char **tw, const signed char *W, double *uk, signed char *wk)
+static void alg4(const geom_t *G, double **tu, signed char **tw, unsigned char **te, const signed char *W, double *uk,
+                 signed char *wk)
 {
     long i;
     long tm[3];
@@ -795,10 +802,18 @@ static void alg4(const geom_t *G, double **tu, signed char **tw, const signed ch
                     stride *= nc[k];
                 }
             } else {
-                /* otherwise the minimum; ties keep the lowest subdomain index */
-                best = 0;
-                for (q = 1; q < ncopies; ++q)
-                    if (tu[cidx[q]][lidxs[q]] < tu[cidx[best]][lidxs[best]]) best = q;
+                /* otherwise the minimum of the fine solutions: copies that
+                 * only echo their Step 2 boundary value are not candidates
+                 * unless every copy is one; ties keep the lowest subdomain
+                 * index */
+                int computed = 0;
+                for (q = 0; q < ncopies; ++q)
+                    if (!te[cidx[q]][lidxs[q]]) computed = 1;
+                best = -1;
+                for (q = 0; q < ncopies; ++q) {
+                    if (computed && te[cidx[q]][lidxs[q]]) continue;
+                    if (best < 0 || tu[cidx[q]][lidxs[q]] < tu[cidx[best]][lidxs[best]]) best = q;
+                }
             }
         }
         uk[i] = tu[cidx[best]][lidxs[best]];
@@ -831,6 +846,7 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     double H, delta = INF;
     double *U, *Uprev, *uk, **tu, *uprev, *Chist[4];
     signed char *W, *wk, **tw;
+    unsigned char **te;
     long tilenodes;
     orc_dd_stats S0;
     theta_ctx tctx;
@@ -867,9 +883,11 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     wk = calloc((size_t)(3 * G.N), 1);
     tu = malloc(sizeof(double *) * (size_t)ntiles);
     tw = malloc(sizeof(signed char *) * (size_t)ntiles);
+    te = malloc(sizeof(unsigned char *) * (size_t)ntiles);
     for (i = 0; i < ntiles; ++i) {
         tu[i] = malloc(sizeof(double) * (size_t)tilenodes);
         tw[i] = malloc((size_t)(3 * tilenodes));
+        te[i] = malloc((size_t)tilenodes);
     }
     for (i = 0; i < G.N; ++i) U[i] = uk[i] = NAN;
 
@@ -904,14 +922,14 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
         for (t[2] = 0; t[2] < G.T[2]; ++t[2])
             for (t[1] = 0; t[1] < G.T[1]; ++t[1])
                 for (t[0] = 0; t[0] < G.T[0]; ++t[0]) {
-                    long s = step23_tile(&G, t, p->h, r, gamma, g, U, W, tu[ti], tw[ti], p->max_fsm_sweeps,
+                    long s = step23_tile(&G, t, p->h, r, gamma, g, U, W, tu[ti], tw[ti], te[ti], p->max_fsm_sweeps,
                                          &S0.fsm_cap_hits);
                     if (s > S0.fsm_sweeps_max) S0.fsm_sweeps_max = s;
                     S0.fine_updates += (long long)s * tilenodes;
                     ++ti;
                 }
         /* Alg. 4 */
-        alg4(&G, tu, tw, W, uk, wk);
+        alg4(&G, tu, tw, te, W, uk, wk);
         S0.iters = it;
         if (it == p->max_iter) break;
         if (it >= 1 && delta < p->tol) {
@@ -989,9 +1007,11 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     for (i = 0; i < ntiles; ++i) {
         free(tu[i]);
         free(tw[i]);
+        free(te[i]);
     }
     free(tu);
     free(tw);
+    free(te);
     free(U);
     free(Uprev);
     free(uprev);

@@ -53,6 +53,10 @@ __host__ __device__ __forceinline__ uint8_t wind_pack(int wx, int wy, int wz = 0
 }
 __host__ __device__ __forceinline__ int wind_comp(uint8_t w, int a) { return (int)((w >> (2 * a)) & 3) - 1; }
 constexpr uint8_t WIND_ZERO = 0x15;  // (0,0,0)
+// Flag on a subdomain's copy of a coarse-set node (never on W or w^k): the node
+// was inflow and the subdomain solve kept its Step 2 value U, so the copy
+// echoes boundary data rather than a fine solution.
+constexpr uint8_t WIND_ECHO = 0x80;
 
 // 2-D Godunov local solve.  vm*/vp* are the neighbours on the minus/plus side
 // of each axis (+inf where missing: the one-sided rule of Sec. 1.1).  Returns

@@ -567,7 +567,7 @@ __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int 
         } else {
             size_t ca2;
             if (tile_inflow(A, xl, yl, X, Y, ca2) && uv == A.U[ca]) {
-                w = A.W[ca];  // inflow value kept: the coarse wind
+                w = A.W[ca] | WIND_ECHO;  // inflow value kept: the coarse wind
             } else if (uv < INF) {
                 T vmx = xl > 0 ? __ldcg(ut + box_index(xl - 1, yl, NY)) : INF;
                 T vpx = xl + 1 < NX ? __ldcg(ut + box_index(xl + 1, yl, NY)) : INF;
@@ -643,14 +643,23 @@ __device__ void alg4_body(const DDArgs<T> &A, int k, size_t bid, size_t nbid) {
             if (ok) {
                 best = sel;
             } else {
-                // minimum; ties keep the lowest subdomain index (slot order)
-                best = 0;
-                T bv = A.cu[a];
-                for (int s = 1; s < 4; ++s) {
+                // minimum of the fine solutions: copies that echo their Step 2
+                // value are candidates only if every copy does; ties keep the
+                // lowest subdomain index (slot order)
+                bool computed = false;
+                for (int s = 0; s < 4; ++s) {
                     if ((s & 1) && !bxi) continue;
                     if ((s & 2) && !byi) continue;
+                    if (!(A.cw[(size_t)s * G.coarse_elems + a] & WIND_ECHO)) computed = true;
+                }
+                best = -1;
+                T bv = T(0);
+                for (int s = 0; s < 4; ++s) {
+                    if ((s & 1) && !bxi) continue;
+                    if ((s & 2) && !byi) continue;
+                    if (computed && (A.cw[(size_t)s * G.coarse_elems + a] & WIND_ECHO)) continue;
                     const T v = A.cu[(size_t)s * G.coarse_elems + a];
-                    if (v < bv) {
+                    if (best < 0 || v < bv) {
                         bv = v;
                         best = s;
                     }
@@ -658,7 +667,7 @@ __device__ void alg4_body(const DDArgs<T> &A, int k, size_t bid, size_t nbid) {
             }
         }
         const T ukv = A.cu[(size_t)best * G.coarse_elems + a];
-        const uint8_t wkv = A.cw[(size_t)best * G.coarse_elems + a];
+        const uint8_t wkv = A.cw[(size_t)best * G.coarse_elems + a] & (uint8_t)~WIND_ECHO;
         const T uold = A.uk[a];  // u^{k-1} (meaningful for k >= 1)
         A.uk[a] = ukv;
         A.wk[a] = wkv;

@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(BOX3_THREADS, 1) k3_fine(DD3Args<T> A) {
         const long long ca = coarse_addr3(A, Xg[0], Xg[1], Xg[2]);
         uint8_t w = WIND_ZERO;
         if (fx[q] == 2 && uv == A.U[ca]) {
-            w = A.W[ca];  // inflow value kept: the coarse wind
+            w = A.W[ca] | WIND_ECHO;  // inflow value kept: the coarse wind
         } else if (fx[q] != 1 && uv < INF) {
             T vm[3], vp[3];
             vm[0] = l[0] > 0 ? su[q - 1] : INF;
@@ -542,12 +542,19 @@ __global__ void k3_alg4(DD3Args<T> A) {
             if (ok) {
                 best = sel;
             } else {
-                // minimum; ties keep the lowest subdomain index (slot order)
-                T bv = A.cu[a];
-                for (int s = 1; s < 8; ++s) {
+                // minimum of the fine solutions: copies that echo their Step 2
+                // value are candidates only if every copy does; ties keep the
+                // lowest subdomain index (slot order)
+                bool computed = false;
+                for (int s = 0; s < 8; ++s)
+                    if (!(s & ~B) && !(A.cw[(size_t)s * G.nc + a] & WIND_ECHO)) computed = true;
+                best = -1;
+                T bv = T(0);
+                for (int s = 0; s < 8; ++s) {
                     if (s & ~B) continue;
+                    if (computed && (A.cw[(size_t)s * G.nc + a] & WIND_ECHO)) continue;
                     const T v = A.cu[(size_t)s * G.nc + a];
-                    if (v < bv) {
+                    if (best < 0 || v < bv) {
                         bv = v;
                         best = s;
                     }
@@ -555,7 +562,7 @@ __global__ void k3_alg4(DD3Args<T> A) {
             }
         }
         const T ukv = A.cu[(size_t)best * G.nc + a];
-        const uint8_t wkv = A.cw[(size_t)best * G.nc + a];
+        const uint8_t wkv = A.cw[(size_t)best * G.nc + a] & (uint8_t)~WIND_ECHO;
         A.uk[a] = ukv;
         A.wk[a] = wkv;
         const size_t f = fidx(A, Xg[0], Xg[1], Xg[2]);

@@ -105,8 +105,9 @@ def test_dd_fp64_bitwise(gpu, n, tiles, c, theta, kmax):
 def test_dd_obstacles_fp64_bitwise(gpu, name, kw, ks):
     """Sec. 4 obstacle and random workloads (subdomain boundary values that
     the subdomain solve must lower): bitwise equal to the oracle, and at 30
-    iterations on the fine solution u^f within 1e-8 (with the 8-sweep cap on
-    Step 4 the fast strip settles 1.4e-9 away from u^f)."""
+    iterations within 1e-6 of the fine solution u^f (with the 8-sweep cap on
+    Step 4 used here the oracle is 1.4e-9 away on the strips, 4e-13 on the
+    maze and 7e-8 on the checkerboard)."""
     w = getattr(I, "workload_" + name)(**kw)
     args = (_t(w["r"], torch.float64), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float64), w["h"],
             w["tiles"], w["c"])
@@ -117,7 +118,7 @@ def test_dd_obstacles_fp64_bitwise(gpu, name, kw, ks):
         assert st["iters"] == s_ref["iters"] == k
         np.testing.assert_array_equal(u.cpu().numpy(), u_ref, err_msg="%s k=%d" % (name, k))
     uf, _, _ = O.fsm(w["r"], w["gamma"], w["g"], w["h"])
-    assert _rel(u.cpu().numpy(), uf) < 1e-8
+    assert _rel(u.cpu().numpy(), uf) < 1e-6
 
 
 def test_dd_fp64_tol_stop_and_stats(gpu):
