@@ -3,11 +3,14 @@
 Workload (default): 2-D 4097^2 grid (h = 1/4096), slowness r = clip(1 + 0.3x +
 0.4 F/max|F|, 0.2) with F a sum of 32 seeded Fourier modes, |k| in [64, 128]
 (eps = 1/64); Gamma = the whole left edge x = 0, g = 0; 16 x 16 subdomains,
-coarse ratio 16 (coarse grid 257^2); FP32 storage; the per-node weight of
-Sec. 4.2 (omega = (1, 1, 1), sigmoid damping gamma 0.75, delta 0.01, x0 0.9,
-capped at 0.3; constant 0.2 where the estimate is undefined); stop when the
-coarse update falls below 1e-6 or after 2*16 + 10 = 42 iterations.
---theta 0.2 runs the constant-weight iteration of Sec. 3.2 instead.
+coarse ratio 16 (coarse grid 257^2); FP32 storage; weight theta = 0 (the
+fastest weight measured on this workload: Step 4 then hands u^k to the causal
+sweep); stop when the coarse update falls below 1e-6 or after 2*16 + 10 = 42
+iterations.  --theta X runs another constant weight, --theta adaptive the
+per-node weight of Sec. 4.2 (omega = (1, 1, 1), sigmoid damping gamma 0.75,
+delta 0.01, x0 0.9, capped at 0.1, constant 0.1 where undefined).  The line
+also carries the time to solution of the adaptive weight and of the constant
+weights 0.05 and 0.2 under the same stop rule.
 
 One step = one complete eik_dd_solve (set-up, Step 1, all parareal iterations)
 on device-resident inputs.  value = local Godunov solves executed per second
@@ -43,8 +46,9 @@ METRIC = "time-to-solution & Gcell-updates/s vs plain GPU full-grid FSM at equal
 N_SIDE = 4097
 TILES = 16
 COARSE = 16
-THETA = 0.2          # constant weight, and the fallback of the adaptive weight
-THETA_CAP = 0.3      # cap on the adaptive weight (cap 1 diverges on this workload)
+THETA = 0.1          # fallback of the adaptive weight where its estimate is undefined
+THETA_CAP = 0.1      # cap on the adaptive weight (cap 1 diverges on this workload)
+THETA_SWEEP = ("adaptive", 0.05, 0.2)
 MAX_ITER = 2 * TILES + 10
 TOL = 1e-6
 MAX_COARSE_SWEEPS = 8
@@ -193,9 +197,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--theta", default="adaptive",
-                    help="'adaptive' (per-node weight of Sec. 4.2, the default) or a constant weight")
-    ap.add_argument("--workload", default="dd4097", choices=["dd4097", "batch256", "dd3d257", "tomography1025"],
+    ap.add_argument("--theta", default="0",
+                    help="a constant weight (default 0) or 'adaptive' (the per-node weight of Sec. 4.2)")
+    ap.add_argument("--workload", default="dd4097",
+                    choices=["dd4097", "batch256", "dd3d257", "tomography1025", "obstacles"],
                     help="dd4097 (default) is the benchmark line; the others measure the batched solve, the "
                          "3-D solve and the tomography gradient with the same keys")
     args = ap.parse_args()
@@ -321,21 +326,45 @@ def main():
             sweeps = eik.FsmStats.from_buffer_copy(bytes(ss.cpu().numpy())).sweeps
             return uu, min(reps), sweeps
 
-        # smallest FP32 FSM sweep count whose error is at most the DD error
-        lo, hi = 1, fst["sweeps"]
+        # smallest FP32 FSM sweep count whose error is at most the DD error; when
+        # the DD is more accurate than the converged FP32 FSM, the FSM's own
+        # converged error is the target (its time to convergence)
+        uu_full, t_full, full_sweeps = fsm_timed(100000)
+        target = max(dd_err, rel_err(uu_full))
+        lo, hi = 1, full_sweeps
         while lo < hi:
             mid = (lo + hi) // 2
             uu, _ = eik.fsm(R, G, g, h, max_sweeps=mid)
-            if rel_err(uu) <= dd_err:
+            if rel_err(uu) <= target:
                 hi = mid
             else:
                 lo = mid + 1
         uu_eq, t_eq, _ = fsm_timed(lo)
-        uu_full, t_full, full_sweeps = fsm_timed(100000)
-        fsm_line = {"sweeps_to_equal_error": lo, "time_to_equal_error_ms": t_eq,
+        fsm_line = {"target_err": target, "sweeps_to_equal_error": lo, "time_to_equal_error_ms": t_eq,
                     "rel_max_err_at_equal": rel_err(uu_eq), "converged_sweeps": full_sweeps,
                     "time_to_convergence_ms": t_full, "rel_max_err_converged": rel_err(uu_full),
                     "dd_over_fsm_time_at_equal_error": ms_per_step / t_eq}
+        # constant weights under the same stop rule (not part of the timed steps)
+        sweep = []
+        for th in THETA_SWEEP:
+            if th == "adaptive":
+                kw = dict(dd_kw, theta=THETA, theta_adaptive=True, theta_cap=THETA_CAP)
+            else:
+                kw = dict(dd_kw, theta=th, theta_adaptive=False)
+            reps = []
+            for rep in range(3):
+                flush.fill_(0.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                uu, ss = eik.dd_solve(R, G, g, h, tiles, COARSE, sync=False, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                reps.append(e0.elapsed_time(e1))
+            s2 = eik.parse_dd_stats(ss)
+            sweep.append({"theta": th, "iters": s2["iters"], "converged": s2["converged"], "ms": min(reps),
+                          "rel_max_err_vs_fp64_fsm": rel_err(uu)})
+        fsm_line["dd_other_theta"] = sweep
     except Exception as e:  # noqa: BLE001
         acc = acc or {"rel_max_err_vs_fp64_fsm": None}
         fsm_line = {"unavailable": str(e)[:160]}
@@ -506,7 +535,10 @@ def run_extra(args):
     elif args.workload == "dd3d257":
         w = inputs.workload_c2()
         R, G, g = t(w["r"].astype(np.float32)), t(w["gamma"]), t(w["g"].astype(np.float32))
-        kw = dict(theta=0.2, max_iter=w["max_iter"], tol=0.0, max_coarse_sweeps=8)
+        kw = dict(theta=THETA, max_iter=w["max_iter"], tol=TOL, max_coarse_sweeps=8)
+        if args.theta == "adaptive":
+            raise SystemExit("the adaptive weight is not built for the 3-D solve")
+        kw["theta"] = float(args.theta)
         grid = eik.make_grid(R, w["h"])
         params = eik.dd_params(w["tiles"], w["c"], **kw)
         ws = torch.empty(eik.eik_dd_workspace_size(grid, params) + 256, dtype=torch.uint8, device=dev)
@@ -582,6 +614,85 @@ def run_extra(args):
             cpu = {"value": cu / dt / 1e9, "unit": unit, "cores": 1, "kind": "oracle",
                    "sample": "Step 1 + one fine pass over all 512 subdomains (max_iter=0), %.1f s" % dt}
         value = upd * world / (ms / 1e3) / 1e9
+    elif args.workload == "obstacles":
+        # Sec. 4 mazes and obstacles / random checkerboard at the paper's sizes:
+        # time to solution (stop at a coarse update below 1e-6, cap 60) of the
+        # DD against the plain FP32 FSM at equal error, each workload solved once
+        # per step
+        ws_ = [inputs.workload_fast_strip(), inputs.workload_maze(), inputs.workload_checkerboard()]
+        kw = dict(theta=THETA, max_iter=60, tol=1e-6, max_coarse_sweeps=8)
+        if args.theta == "adaptive":
+            kw.update(theta_adaptive=True, theta_cap=THETA_CAP)
+        else:
+            kw["theta"] = float(args.theta)
+        cases = []
+        for q in ws_:
+            R, G, g = t(q["r"].astype(np.float32)), t(q["gamma"]), t(q["g"].astype(np.float32))
+            cases.append((q, R, G, g))
+
+        def solve_all():
+            out = []
+            for q, R, G, g in cases:
+                out.append(eik.dd_solve(R, G, g, q["h"], q["tiles"], q["c"], sync=False, **kw))
+            return out
+        prof = _profiled(torch, eik, solve_all)
+        with ClockSampler(local_rank) as clk:
+            ms = _timed(torch, solve_all, args.steps, args.warmup, flush, stream)
+        res = solve_all()
+        torch.cuda.synchronize()
+        per = []
+        upd = 0
+        fine_upd = 0
+        for (q, R, G, g), (u, stt) in zip(cases, res):
+            s2 = eik.parse_dd_stats(stt)
+            upd += s2["fine_updates"] + s2["coarse_updates"]
+            fine_upd += s2["fine_updates"]
+            uf, _ = eik.fsm(R.double(), G, g.double(), q["h"])
+            umax = uf.abs().max().item()
+            err = lambda x: (x.double() - uf).abs().max().item() / umax
+            dd_err = err(u)
+            t_dd = _timed(torch, lambda: eik.dd_solve(R, G, g, q["h"], q["tiles"], q["c"], sync=False, **kw), 3, 1,
+                          flush, stream)
+            uu, fst = eik.fsm(R, G, g, q["h"])
+            target = max(dd_err, err(uu))
+            lo, hi = 1, fst["sweeps"]
+            while lo < hi:
+                mid = (lo + hi) // 2
+                if err(eik.fsm(R, G, g, q["h"], max_sweeps=mid)[0]) <= target:
+                    hi = mid
+                else:
+                    lo = mid + 1
+            t_f = _timed(torch, lambda: eik.fsm(R, G, g, q["h"], max_sweeps=lo, sync=False), 3, 1, flush, stream)
+            per.append({"workload": q["name"], "n": q["r"].shape[0], "tiles": q["tiles"][0], "coarse_ratio": q["c"],
+                        "iters": s2["iters"], "converged": s2["converged"], "dd_ms": t_dd,
+                        "rel_max_err_vs_fp64_fsm": dd_err, "fsm_f32_sweeps_to_equal_error": lo,
+                        "fsm_f32_ms_to_equal_error": t_f, "dd_over_fsm": t_dd / t_f})
+        fine_ms = prof["dd_fine_subdomains"]["total_ms"]
+        kern = ("dd_fine_subdomains", fine_upd * BYTES_PER_UPDATE_F32 / (fine_ms / 1e3) / 1e9)
+        extra = {"per_workload": per}
+        hr = [torch.from_numpy(q["r"].astype(np.float32)).pin_memory() for q, *_ in cases]
+        hu = [torch.empty_like(x).pin_memory() for x in hr]
+
+        def e2e_step():
+            for (q, R, G, g), x in zip(cases, hr):
+                R.copy_(x, non_blocking=True)
+            for (u, _), y in zip(solve_all(), hu):
+                y.copy_(u, non_blocking=True)
+        e2e_ms = _timed(torch, e2e_step, max(1, args.steps // 2), 1, flush, stream)
+        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": sum(x.numel() * 4 for x in hr),
+               "d2h_bytes_per_step": sum(x.numel() * 4 for x in hu), "ms_per_step": e2e_ms}
+        workload = {"workload": "sec4_obstacles_fast_strip501_maze501_checkerboard1401", **kw,
+                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
+        unit, metric = "ms", "Sec. 4 obstacle workloads: DD time to solution, the three solved in sequence"
+        if rank == 0 and not args.no_cpu_baseline:
+            q = ws_[0]
+            t0 = time.perf_counter()
+            _, so, _ = oracle.dd(q["r"].astype(np.float32).astype(np.float64), q["gamma"], q["g"], q["h"],
+                                 q["tiles"], q["c"], **kw)
+            dt = time.perf_counter() - t0
+            cpu = {"value": dt * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+                   "sample": "the fast strip alone, full solve, FP64 (%d iterations)" % so["iters"]}
+        value = ms
     else:
         w = inputs.workload_c4()
         n, h = w["n"], w["h"]
@@ -642,7 +753,7 @@ def run_extra(args):
         value = S * world / (ms / 1e3)
     if rank == 0:
         line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": unit != "ms", "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload,
                 "roofline": {"bound": "hbm", "achieved": kern[1], "peak": peak, "unit": "GB/s",
                              "frac": kern[1] / peak, "traffic": None, "kernel": kern[0], "peak_source": peak_kind,

@@ -151,10 +151,12 @@ size_t eik_dd_workspace_size(const eik_grid *grid, const eik_dd_params *params);
  *   Step 1  every shifted coarse grid (spacing H) solved by FSM with Alg. 1,
  *           then the causal sweep (Alg. 2)                        -> U^0, W^0
  *   repeat for k = 0, 1, ...
- *   Step 2  subdomain boundary data: U where W.n > 0 for an inward normal n,
- *           otherwise free (+inf, one-sided updates); Gamma fixed at g
- *   Step 3  FSM in every subdomain (Alg. 3)                       -> u, w
- *   Alg. 4  u^k, w^k at every coarse-set node from the subdomain copies
+ *   Step 2  subdomain boundary starting values: U where W.n > 0 for an
+ *           inward normal n (inflow), otherwise +inf; Gamma fixed at g
+ *   Step 3  FSM in every subdomain (Alg. 3), boundary nodes included (one-
+ *           sided differences; an inflow value can only decrease) -> u, w
+ *   Alg. 4  u^k, w^k at every coarse-set node from the subdomain copies (the
+ *           minimum, where taken, skips copies that kept their inflow U)
  *           stop if k == max_iter or (k >= 1 and max|U^k - U^{k-1}| < tol)
  *   Step 4  Alg. 5 weighted update U = u^k + theta (U~ - C_H(U^k)) swept on
  *           every shifted grid, W = w^k, then the causal sweep   -> U^{k+1}
