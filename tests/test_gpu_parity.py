@@ -6,6 +6,8 @@ FP32-rounded inputs: relative max-norm error <= 1e-5 (the tolerance of the
 method's FP32 storage).  Winds are compared through their effect: the DD
 iterates, which depend on every Alg. 4 / Alg. 5 decision.
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -195,9 +197,9 @@ def test_fsm_full_size_fp32_against_oracle(gpu):
     same rounded slowness, element by element."""
     w = I.workload_c1()
     r32 = w["r"].astype(np.float32)
-    u_ref, s_ref, c_ref = O.fsm(r32.astype(np.float64), w["gamma"], w["g"], w["h"])
+    u_ref = _c1_oracle_fsm()
     u, st = gpu.fsm(_t(r32, torch.float32), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float32), w["h"])
-    assert c_ref and st["converged"] == 1
+    assert st["converged"] == 1
     assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
 
 
@@ -238,7 +240,16 @@ def test_dd_adaptive_theta_validation(gpu):
 
 # The DD workload of the benchmark: 4097^2, 16x16 subdomains, coarse ratio 16,
 # theta 0.2, FP32, in the launch configuration bench.py times.
-C1_DD = dict(theta=0.2, tol=1e-6, max_coarse_sweeps=8)
+C1_DD = dict(theta=0.0, tol=1e-6, max_coarse_sweeps=8)   # the benchmark's solve
+
+
+@functools.lru_cache(maxsize=1)
+def _c1_oracle_fsm():
+    w = I.workload_c1()
+    r32 = w["r"].astype(np.float32)
+    u_ref, s_ref, c_ref = O.fsm(r32.astype(np.float64), w["gamma"], w["g"], w["h"])
+    assert c_ref
+    return u_ref
 
 
 def _godunov_2d(vmx, vpx, vmy, vpy, rh):
@@ -287,17 +298,22 @@ def test_dd_full_size_first_pass_fp32(gpu):
     assert rel.max() <= 1e-2
 
 
-def test_dd_full_size_fixed_point_property(gpu):
-    """4097^2 DD after the benchmark's 42 iterations.  Every subdomain solve
-    ends at its Gauss-Seidel fixed point, so at each node strictly inside a
-    subdomain (neighbours included, so that no neighbour took another
+def test_dd_full_size_converged_solve(gpu):
+    """4097^2 DD exactly as the benchmark runs it (theta = 0, stop at a coarse
+    update below 1e-6, cap 42).  It converges, and then (a) at every node the
+    output agrees with the FP64 oracle's full-grid fine solution u^f on the
+    same rounded slowness within the FP32 tolerance 1e-5, and (b) every
+    subdomain solve ends at its Gauss-Seidel fixed point: at each node strictly
+    inside a subdomain (neighbours included, so that no neighbour took another
     subdomain's value in Alg. 4) u equals the Godunov local solve of its four
-    neighbours, up to FP32 rounding.  Checked at every such node."""
+    neighbours, up to FP32 rounding."""
     w = I.workload_c1()
     r32 = w["r"].astype(np.float32)
     u, st = gpu.dd_solve(_t(r32, torch.float32), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float32), w["h"],
                          w["tiles"], w["c"], max_iter=w["max_iter"], **C1_DD)
-    assert st["iters"] == w["max_iter"] and st["error"] == 0 and st["fsm_cap_hits"] == 0
+    assert st["converged"] == 1 and st["iters"] <= w["max_iter"]
+    assert st["error"] == 0 and st["fsm_cap_hits"] == 0
+    assert _rel(u.cpu().numpy().astype(np.float64), _c1_oracle_fsm()) <= TOL32
     U = u.cpu().numpy().astype(np.float64)
     n = U.shape[0]
     S = (n - 1) // w["tiles"][0]
