@@ -190,6 +190,22 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (the job's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, total_ms):
+    """Whole-job G units/s: every rank processed units_per_rank in total_ms
+    (the max over ranks)."""
+    return units_per_rank * world / (total_ms / 1e3) / 1e9
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,12 +298,9 @@ def main():
     upd_step = stats["fine_updates"] + stats["coarse_updates"]
     upd_total = upd_step * args.steps
     launches = stats["launches"] * args.steps
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
-    value = upd_total * world / (total_ms / 1e3) / 1e9
+    value = job_throughput(upd_total, world, total_ms)
     cells = float(N_SIDE) * N_SIDE
 
     # roofline of the dominant kernel (event-timed inside the timed region)
