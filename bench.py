@@ -512,7 +512,8 @@ def run_extra(args):
                                "ctas_per_sm": best.ctas_per_sm, "largest_first": best.largest_first,
                                "tune_ms": tune_ms},
                  "launches_per_solve": st[0]["launches"], "graph": True,
-                 "iters": sorted(set(x["iters"] for x in st))}
+                 "iters": sorted(set(x["iters"] for x in st)),
+                 "converged": sum(int(x["converged"]) for x in st)}
         # end to end: pinned host inputs in, every u out, each step
         hr = [torch.from_numpy(q["r"].astype(np.float32)).pin_memory() for q in w]
         hu = [torch.empty_like(x).pin_memory() for x in hr]
@@ -528,7 +529,7 @@ def run_extra(args):
                "d2h_bytes_per_step": h2d, "ms_per_step": e2e_ms,
                "note": "slowness of every problem in, every u out (sources stay resident)"}
         workload = {"workload": "batch_256_mixed_2d", "nprob": len(w), "sides": [257, 513, 1025, 2049],
-                    "tiles": [8, 16, 32], "theta": 0.2, "cap": "2T+10",
+                    "tiles": [8, 16, 32], "theta": w[0]["theta"], "tol": w[0]["tol"], "cap": "2T+10",
                     "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
         unit, metric = "Gupdates/s", "batched DD: local solves per second over a 256-problem mixed batch"
         if rank == 0 and not args.no_cpu_baseline:

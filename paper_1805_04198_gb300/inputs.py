@@ -143,12 +143,14 @@ def workload_c2(n=257, tiles=8, c=8):
                 theta=1.0, max_iter=2 * tiles + 10, tol=0.0)
 
 
-def workload_c3(nprob=256, sides=(257, 513, 1025, 2049), tiles=(8, 16, 32), theta=0.2, seed0=SEED_C3):
+def workload_c3(nprob=256, sides=(257, 513, 1025, 2049), tiles=(8, 16, 32), theta=0.0, tol=1e-6,
+                seed0=SEED_C3):
     """Batch of independent 2-D problems.  Problem p draws from SplitMix64(seed0 + p):
     side n ~ U(sides), subdomains per side T ~ U(tiles), eps ~ U[16h, 64h] with
     h = 1/(n-1), a seed for its Fourier-mode slowness (as for the 4097^2
     workload, |k| in [1/eps, 2/eps]) and a point source at a uniformly drawn
-    interior node.  Coarse ratio c = min(8, (n-1)/T); iteration cap 2T + 10."""
+    interior node.  Coarse ratio c = min(8, (n-1)/T); iteration cap 2T + 10,
+    stop when the coarse update falls below tol; weight theta."""
     out = []
     for p in range(nprob):
         rng = SplitMix64(seed0 + p)
@@ -162,7 +164,7 @@ def workload_c3(nprob=256, sides=(257, 513, 1025, 2049), tiles=(8, 16, 32), thet
         gamma, g = point_source((n, n), (sy, sx))
         S = (n - 1) // T
         out.append(dict(name="c3_p%d_%d_T%d" % (p, n, T), r=r, gamma=gamma, g=g, h=h, tiles=(T, T),
-                        c=min(8, S), theta=theta, max_iter=2 * T + 10, tol=0.0))
+                        c=min(8, S), theta=theta, max_iter=2 * T + 10, tol=tol))
     return out
 
 
