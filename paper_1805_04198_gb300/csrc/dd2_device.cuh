@@ -715,7 +715,7 @@ __device__ void alg4_body(const DDArgs<T> &A, int k, size_t bid, size_t nbid) {
             A.uk_sk[si] = ukv;
             A.mask_sk[si] = m;
             A.cold_sk[si] = cold;
-            if (A.adaptive) A.theta_sk[si] = th;
+            if (A.theta_sk) A.theta_sk[si] = th;  // per-node or (in a mixed batch) constant weight
         }
     }
 }

@@ -249,17 +249,20 @@ __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, 
     }
 EIK_BATCH_PAIR(kb_step1, k_step1_body, 96, 224)
 EIK_BATCH_PAIR(kb_step4, k_step4_body, 160, 224)
+EIK_BATCH_PAIR(kb_step4a, k_step4a_body, 160, 224)
 EIK_BATCH_PAIR(kb_fine, k_fine_body, 96, 224)
 
 template <class T> struct BatchKernels;
 template <> struct BatchKernels<float> {
     static constexpr void (*step1)(const DDArgs<float> *, ItemList) = kb_step1_f32;
     static constexpr void (*step4)(const DDArgs<float> *, ItemList) = kb_step4_f32;
+    static constexpr void (*step4a)(const DDArgs<float> *, ItemList) = kb_step4a_f32;
     static constexpr void (*fine)(const DDArgs<float> *, ItemList) = kb_fine_f32;
 };
 template <> struct BatchKernels<double> {
     static constexpr void (*step1)(const DDArgs<double> *, ItemList) = kb_step1_f64;
     static constexpr void (*step4)(const DDArgs<double> *, ItemList) = kb_step4_f64;
+    static constexpr void (*step4a)(const DDArgs<double> *, ItemList) = kb_step4a_f64;
     static constexpr void (*fine)(const DDArgs<double> *, ItemList) = kb_fine_f64;
 };
 
@@ -289,6 +292,8 @@ struct BatchPlan {
     int nq = 0;
     size_t bytes = 0;
     int max_iter = 0;
+    bool adaptive = false;  // some problem uses the per-node weight: every problem
+                            // carries the weight as a fourth Alg. 5 static
 };
 
 static const eik_dd_batch_config kDefaultConfig = {0, 0, 0, 1};
@@ -309,10 +314,6 @@ static bool batch_validate(int nprob, const eik_grid *grids, const eik_dd_params
         }
         if (grids[p].dtype != grids[0].dtype) {
             set_error("problem %d: every problem of a batch must have the same dtype", p);
-            return false;
-        }
-        if (params[p].theta_adaptive) {
-            set_error("problem %d: the batched solve takes a constant theta (theta_adaptive = 0)", p);
             return false;
         }
         if (!dd_validate(&grids[p], &params[p])) {
@@ -339,8 +340,12 @@ static void batch_plan(int nprob, const eik_grid *grids, const eik_dd_params *pa
     B.P.resize(nprob);
     B.tab.clear();
     B.max_iter = 0;
+    B.adaptive = false;
+    for (int p = 0; p < nprob; ++p) B.adaptive = B.adaptive || params[p].theta_adaptive != 0;
     for (int p = 0; p < nprob; ++p) {
-        B.P[p] = dd_plan(&grids[p], &params[p]);
+        eik_dd_params q = params[p];
+        if (B.adaptive) q.theta_adaptive = 1;  // storage and Step 4 shape of the weighted form
+        B.P[p] = dd_plan(&grids[p], &q);
         B.max_iter = std::max(B.max_iter, params[p].max_iter);
     }
     auto push_prefix = [&](auto count) -> int {
@@ -463,7 +468,14 @@ static int batch_run(int nprob, const eik_grid *grids, const void *const *r, con
         A.max_iter = params[p].max_iter;
         A.max_fsm = params[p].max_fsm_sweeps;
         A.max_coarse = params[p].max_coarse_sweeps;
+        A.adaptive = params[p].theta_adaptive ? 1 : 0;
+        for (int s2 = 0; s2 < 3; ++s2) A.om[s2] = params[p].omega[s2];
+        A.sg = params[p].sig_gamma;
+        A.sd = params[p].sig_delta;
+        A.sx0 = params[p].sig_x0;
+        A.cap = params[p].theta_cap;
     }
+    auto step4k = B.adaptive ? BatchKernels<T>::step4a : BatchKernels<T>::step4;
     const DDArgs<T> *dargs = reinterpret_cast<const DDArgs<T> *>(base + B.args_off);
     const int *dtab = reinterpret_cast<const int *>(base + B.tab_off);
     int *ctl = reinterpret_cast<int *>(base + B.ctl_off);
@@ -492,7 +504,7 @@ static int batch_run(int nprob, const eik_grid *grids, const void *const *r, con
     if ((rc = cuda_check(cudaFuncSetAttribute(BatchKernels<T>::step1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)std::max<size_t>(need_grid, 1)), "smem attr step1")))
         return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(BatchKernels<T>::step4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((rc = cuda_check(cudaFuncSetAttribute(step4k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)std::max<size_t>(need_grid, 1)), "smem attr step4")))
         return rc;
 
@@ -563,7 +575,7 @@ static int batch_run(int nprob, const eik_grid *grids, const void *const *r, con
         if (k == B.max_iter) break;
         for (const BoxClass &c : B.grid) {
             EIK_LAUNCH("dd_step4_weighted", s,
-                       BatchKernels<T>::step4<<<ctas(BatchKernels<T>::step4, c, gq), 32 * c.nw, c.smem, s>>>(dargs, item_list(c, gq)));
+                       step4k<<<ctas(step4k, c, gq), 32 * c.nw, c.smem, s>>>(dargs, item_list(c, gq)));
             ++nl;
         }
         if ((rc = launch_causal(1))) return rc;

@@ -398,7 +398,9 @@ class DDBatch:
 
     problems: list of dicts with keys r, gamma, g (device tensors, r and g of
     one float dtype for the whole batch), h, tiles, coarse_ratio and optionally
-    theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps.  Owns the outputs
+    theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps and the per-node
+    weight's theta_adaptive, omega, sig_gamma, sig_delta, sig_x0, theta_cap
+    (see dd_params).  Owns the outputs
     `u` (list), the workspace and the device statistics.  run() enqueues one
     batched solve; capture() records it into a CUDA graph that replay() reruns."""
 
@@ -413,8 +415,10 @@ class DDBatch:
             if gm.dtype != torch.uint8 or gm.shape != r.shape:
                 raise ValueError("gamma must be uint8 with r's shape")
         self.grids = [make_grid(p["r"], p["h"]) for p in problems]
+        adaptive_keys = ("theta_adaptive", "omega", "sig_gamma", "sig_delta", "sig_x0", "theta_cap")
         self.params = [dd_params(p["tiles"], p["coarse_ratio"], p.get("theta", 1.0), p.get("max_iter", 10),
-                                 p.get("tol", 0.0), p.get("max_fsm_sweeps", 100000), p.get("max_coarse_sweeps", 8))
+                                 p.get("tol", 0.0), p.get("max_fsm_sweeps", 100000), p.get("max_coarse_sweeps", 8),
+                                 **{k: p[k] for k in adaptive_keys if k in p})
                        for p in problems]
         nbytes = eik_dd_batched_workspace_size(self.grids, self.params)
         if nbytes == 0:

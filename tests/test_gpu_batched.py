@@ -220,3 +220,35 @@ def test_batched_full_size_sampled(gpu):
         fin = np.isfinite(u_ref)
         assert np.array_equal(np.isfinite(a), fin)
         assert np.max(np.abs(a[fin] - u_ref[fin])) / np.max(np.abs(u_ref[fin])) <= 1e-5
+
+
+_ADAPT = ("theta_adaptive", "omega", "sig_gamma", "sig_delta", "sig_x0", "theta_cap")
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_adaptive_weight_mixed(gpu, dtype):
+    """A batch mixing problems with the per-node weight of Sec. 4.2 and
+    problems with a constant weight (every problem then carries the weight as
+    a fourth Alg. 5 static): each output equals its own single-problem solve
+    bitwise, with the same statistics, under the default and two explicit
+    launch configurations."""
+    probs = _mixed(dtype)
+    for i in (0, 4, 6):
+        probs[i].update(theta_adaptive=True, theta_cap=0.5, omega=(1.0, 0.5, 0.25))
+    singles = []
+    for p in probs:
+        kw = {k: p[k] for k in _ADAPT if k in p}
+        singles.append(gpu.dd_solve(p["r"], p["gamma"], p["g"], p["h"], p["tiles"], p["coarse_ratio"],
+                                    theta=p["theta"], max_iter=p["max_iter"], tol=p["tol"], max_coarse_sweeps=8,
+                                    **kw))
+    B = gpu.DDBatch(probs)
+    for cfg in (None, gpu.BatchConfig(1, 1, 0, 1), gpu.BatchConfig(0, 0, 1, 0)):
+        B.config = cfg
+        for u in B.u:
+            u.fill_(float("nan"))
+        B.run()
+        stats = B.stats()
+        for i, (u1, s1) in enumerate(singles):
+            assert torch.equal(B.u[i], u1), i
+            for key in ("iters", "converged", "fine_updates", "coarse_updates", "coarse_cap_hits"):
+                assert stats[i][key] == s1[key], (i, key)
