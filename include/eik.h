@@ -119,7 +119,7 @@ typedef struct {
     int64_t max_fsm_sweeps;    /* cap per subdomain solve (Step 3) */
     int64_t max_coarse_sweeps; /* cap per coarse-grid solve (Steps 1 and 4) */
     /* Per-node weight (Sec. 4.2) instead of the constant theta when
-     * theta_adaptive != 0 (2-D single-problem solves): the bound of Theorem 2
+     * theta_adaptive != 0 (2-D, 3-D and batched solves): the bound of Theorem 2
      * estimated by eq. secthetaest, (u^k - u^{k-1}) over the weighted mean of
      * the last (up to three) changes of C_H(nbrs U), damped by eq. thetaest
      * [s t + (1 - s) delta t]^+ with s = 1 / (1 + exp((t - x0) / gamma)), and

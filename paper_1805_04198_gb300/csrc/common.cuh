@@ -177,4 +177,26 @@ __device__ inline bool grid_barrier(unsigned *bar, int *err) {
     return ok;
 }
 
+// Per-node weight of Sec. 4.2 from du = u^k - u^{k-1} and the last n changes
+// dC[s] of C_H(nbrs U): eq. secthetaest (weighted mean of the changes), the
+// damping of eq. thetaest, the optional cap; `fallback` where undefined.  A is
+// any argument block carrying the weights om[3] and the damping parameters sg
+// (gamma), sd (delta), sx0 (x0) and cap.
+template <class Args>
+__device__ inline double theta_estimate(const Args &A, double du, const double *dC, int n, double fallback) {
+    double den = 0.0, wsum = 0.0;
+    for (int s = 0; s < n; ++s) {
+        den = __dadd_rn(den, __dmul_rn(A.om[s], dC[s]));
+        wsum = __dadd_rn(wsum, A.om[s]);
+    }
+    if (!(wsum > 0.0)) return fallback;
+    den = __ddiv_rn(den, wsum);
+    const double t = __ddiv_rn(du, den);
+    if (!isfinite(t) || den == 0.0) return fallback;
+    const double sig = __ddiv_rn(1.0, __dadd_rn(1.0, exp(__ddiv_rn(__dsub_rn(t, A.sx0), A.sg))));
+    double v = __dadd_rn(__dmul_rn(sig, t), __dmul_rn(__dmul_rn(__dsub_rn(1.0, sig), A.sd), t));
+    if (A.cap > 0.0 && v > A.cap) v = A.cap;
+    return v > 0.0 ? v : 0.0;
+}
+
 }  // namespace eik

@@ -69,6 +69,19 @@ bool dd3_validate(const eik_grid *grid, const eik_dd_params *p);
 int dd3_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, const eik_dd_params *p,
             void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s);
 
+// Parameters of the per-node weight of Sec. 4.2 (2-D and 3-D).
+static bool valid_adaptive(const eik_dd_params *p) {
+    if (!p->theta_adaptive) return true;
+    const double w = p->omega[0] + p->omega[1] + p->omega[2];
+    bool ok = std::isfinite(p->sig_delta) && std::isfinite(p->sig_x0) && std::isfinite(p->theta_cap) &&
+              p->sig_gamma > 0.0 && std::isfinite(p->sig_gamma) && w > 0.0 && std::isfinite(w);
+    for (int s2 = 0; s2 < 3; ++s2) ok = ok && p->omega[s2] >= 0.0;
+    if (!ok)
+        set_error("adaptive theta: omega must be >= 0 with a positive finite sum, sig_gamma > 0, "
+                  "sig_delta, sig_x0 and theta_cap finite");
+    return ok;
+}
+
 bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
     if (!p) {
         set_error("params is NULL");
@@ -76,16 +89,12 @@ bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
     }
     if (grid && grid->ndim == 3) {
         if (!valid_grid_common(grid, 3)) return false;
-        if (p->theta_adaptive) {
-            set_error("the per-node weight (theta_adaptive) is implemented for 2-D grids");
-            return false;
-        }
         if (p->max_iter < 0 || p->max_iter > 100000 || p->max_fsm_sweeps < 1 || p->max_coarse_sweeps < 1 ||
             p->max_fsm_sweeps > MAX_SWEEPS || p->max_coarse_sweeps > MAX_SWEEPS || !std::isfinite(p->theta)) {
             set_error("max_iter must be in [0, 100000], sweep caps in [1, %lld], theta finite", MAX_SWEEPS);
             return false;
         }
-        return dd3_validate(grid, p);
+        return valid_adaptive(p) && dd3_validate(grid, p);
     }
     if (!valid_grid_common(grid, 2)) return false;
     for (int a = 0; a < 2; ++a) {
@@ -123,18 +132,7 @@ bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
         set_error("theta must be finite");
         return false;
     }
-    if (p->theta_adaptive) {
-        const double w = p->omega[0] + p->omega[1] + p->omega[2];
-        bool ok = std::isfinite(p->sig_delta) && std::isfinite(p->sig_x0) && std::isfinite(p->theta_cap) &&
-                  p->sig_gamma > 0.0 && std::isfinite(p->sig_gamma) && w > 0.0 && std::isfinite(w);
-        for (int s2 = 0; s2 < 3; ++s2) ok = ok && p->omega[s2] >= 0.0;
-        if (!ok) {
-            set_error("adaptive theta: omega must be >= 0 with a positive finite sum, sig_gamma > 0, "
-                      "sig_delta, sig_x0 and theta_cap finite");
-            return false;
-        }
-    }
-    return true;
+    return valid_adaptive(p);
 }
 
 template <class T>

@@ -61,6 +61,13 @@ struct DD3Args {
     T theta, tol;
     int max_iter;
     long long max_fsm, max_coarse;
+    // per-node weight of Sec. 4.2 (adaptive = 1): weights, damping, cap, the
+    // last four C_H(nbrs U) (slot m % 4), du = u^k - u^{k-1}, the weight
+    int adaptive;
+    double om[3], sg, sd, sx0, cap;
+    T *Ch[4];
+    double *du;
+    T *th;
 };
 
 template <class T>
@@ -247,13 +254,14 @@ struct Alg5_3 {
     const uint8_t *mask;
     long long off;
     T Hs, theta;
+    const T *th;  // per-node weight (nullptr: the constant theta)
     struct Stat {
-        T rc, uk, cold;
+        T rc, uk, cold, th;
         uint8_t m;
     };
     __device__ __forceinline__ Stat load(int, int, int, int idx) const {
         const long long a = off + idx;
-        return Stat{rc[a], uk[a], cold[a], mask[a]};
+        return Stat{rc[a], uk[a], cold[a], th ? th[a] : theta, mask[a]};
     }
     __device__ __forceinline__ void fill(Stat &, int) const {}
     __device__ __forceinline__ T apply(T self, const T *vm, const T *vp, const Stat &st, int,
@@ -270,7 +278,7 @@ struct Alg5_3 {
             const int wc = wind_comp(w, ax);
             pass = pass && ((wc <= 0 && (m & (2 << (2 * ax)))) || (wc >= 0 && (m & (4 << (2 * ax)))));
         }
-        const T nu = pass ? N::add(ukv, N::mul(theta, N::sub(Ut, cv))) : ukv;
+        const T nu = pass ? N::add(ukv, N::mul(st.th, N::sub(Ut, cv))) : ukv;
         changed = !(nu == self);
         return nu;
     }
@@ -362,7 +370,7 @@ __global__ void __launch_bounds__(BOX3_THREADS, 1) k3_step1(DD3Args<T> A) {
 
 // Step 4: Alg. 5 on every shifted grid.
 template <class T>
-__global__ void __launch_bounds__(BOX3_THREADS, 1) k3_step4(DD3Args<T> A) {
+__global__ void __launch_bounds__(BOX3_THREADS, 1) k3_step4(DD3Args<T> A, int k) {
     if (*A.done) return;
     extern __shared__ __align__(16) char smem[];
     const Grid3 d = A.grids[blockIdx.x];
@@ -389,13 +397,29 @@ __global__ void __launch_bounds__(BOX3_THREADS, 1) k3_step4(DD3Args<T> A) {
         vp[2] = z + 1 < d.mz ? su[q + ps] : INF;
         const T rv = A.rc[a];
         uint8_t w;
-        A.cold[a] = local_solve3(vm, vp, Num<T>::mul(rv > T(0) ? rv : T(0), Hs), w);
+        const T cold = local_solve3(vm, vp, Num<T>::mul(rv > T(0) ? rv : T(0), Hs), w);
+        A.cold[a] = cold;
+        if (A.adaptive) {
+            // Sec. 4.2 with every term lagged as in eq. firstthetaest
+            double thv = (double)A.theta;
+            if (k >= 1) {
+                const int nt = k < 3 ? k : 3;
+                const T *c1 = A.Ch[(k + 3) & 3], *c2 = A.Ch[(k + 2) & 3], *c3 = A.Ch[(k + 1) & 3];
+                double dC[3] = {0.0, 0.0, 0.0};
+                dC[0] = __dsub_rn((double)cold, (double)c1[a]);
+                if (nt > 1) dC[1] = __dsub_rn((double)c1[a], (double)c2[a]);
+                if (nt > 2) dC[2] = __dsub_rn((double)c2[a], (double)c3[a]);
+                thv = theta_estimate(A, A.du[a], dC, nt, (double)A.theta);
+            }
+            A.Ch[k & 3][a] = cold;
+            A.th[a] = (T)thv;
+        }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += blockDim.x) su[sq(e)] = A.U0[d.off + e];  // Sec. 1.1 initialisation
     __threadfence_block();
     __syncthreads();
-    Alg5_3<T> pol{A.rc, A.uk, A.cold, A.mask, d.off, Hs, A.theta};
+    Alg5_3<T> pol{A.rc, A.uk, A.cold, A.mask, d.off, Hs, A.theta, A.adaptive ? A.th : nullptr};
     long long sweeps;
     bool conv;
     box3_sweeps(su, d.mx, d.my, d.mz, pol, A.max_coarse, sweeps, conv);
@@ -563,6 +587,7 @@ __global__ void k3_alg4(DD3Args<T> A) {
         }
         const T ukv = A.cu[(size_t)best * G.nc + a];
         const uint8_t wkv = A.cw[(size_t)best * G.nc + a] & (uint8_t)~WIND_ECHO;
+        if (A.adaptive) A.du[a] = __dsub_rn((double)ukv, (double)A.uk[a]);  // u^k - u^{k-1}
         A.uk[a] = ukv;
         A.wk[a] = wkv;
         const size_t f = fidx(A, Xg[0], Xg[1], Xg[2]);
@@ -725,6 +750,7 @@ struct DD3Plan {
     std::vector<int> offmap;
     size_t fine_smem, grid_smem, bytes;
     int fine_threads, grid_threads;
+    bool adaptive;
 };
 
 static bool dd3_plan(const eik_grid *grid, const eik_dd_params *p, DD3Plan &P) {
@@ -738,6 +764,7 @@ static bool dd3_plan(const eik_grid *grid, const eik_dd_params *p, DD3Plan &P) {
     G.c = c;
     G.h = grid->h;
     G.H = (double)c * grid->h;
+    P.adaptive = p->theta_adaptive != 0;
     P.grids.clear();
     P.offmap.assign((size_t)c * c * c, -1);
     long long off = 0;
@@ -786,7 +813,17 @@ static size_t dd3_layout(const DD3Plan &P, DD3Args<T> *A, void *ws, int max_iter
     int *chg = cv.take<int>(4);
     unsigned *bar = cv.take<unsigned>(4);
     DevStats3 *st = cv.take<DevStats3>(1);
+    T *Ch[4] = {nullptr, nullptr, nullptr, nullptr}, *th = nullptr;
+    double *du = nullptr;
+    if (P.adaptive) {
+        for (int s = 0; s < 4; ++s) Ch[s] = cv.take<T>(G.nc);
+        th = cv.take<T>(G.nc);
+        du = cv.take<double>(G.nc);
+    }
     if (A) {
+        for (int s = 0; s < 4; ++s) A->Ch[s] = Ch[s];
+        A->th = th;
+        A->du = du;
         A->U = U; A->Uprev = Uprev; A->U0 = U0; A->rc = rc; A->uk = uk; A->cold = cold;
         A->W = W; A->wk = wk; A->mask = mask; A->cu = cu; A->cw = cw;
         A->grids = grids; A->offmap = offmap; A->done = done; A->deltas = deltas; A->chg = chg; A->bar = bar;
@@ -868,6 +905,12 @@ static int dd3_run_t(const eik_grid *grid, const void *r, const uint8_t *gamma, 
     A.max_iter = p->max_iter;
     A.max_fsm = p->max_fsm_sweeps;
     A.max_coarse = p->max_coarse_sweeps;
+    A.adaptive = P.adaptive ? 1 : 0;
+    for (int s2 = 0; s2 < 3; ++s2) A.om[s2] = p->omega[s2];
+    A.sg = p->sig_gamma;
+    A.sd = p->sig_delta;
+    A.sx0 = p->sig_x0;
+    A.cap = p->theta_cap;
     const DD3Geom &G = P.G;
     int rc, dev, nsm = 0, optin = 0;
     if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
@@ -913,7 +956,7 @@ static int dd3_run_t(const eik_grid *grid, const void *r, const uint8_t *gamma, 
         EIK_LAUNCH("dd3_alg4_restrict", s, k3_alg4<T><<<cgrid, ew, 0, s>>>(A)); ++nl;
         EIK_LAUNCH("dd3_check", s, k3_check<T><<<1, 1, 0, s>>>(A, k)); ++nl;
         if (k == p->max_iter) break;
-        EIK_LAUNCH("dd3_step4_weighted", s, k3_step4<T><<<G.ng, P.grid_threads, P.grid_smem, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd3_step4_weighted", s, k3_step4<T><<<G.ng, P.grid_threads, P.grid_smem, s>>>(A, k)); ++nl;
         if ((rc = launch_causal(1))) return rc;
         EIK_LAUNCH("dd3_delta", s, k3_delta<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
     }

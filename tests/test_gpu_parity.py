@@ -235,11 +235,32 @@ def test_dd_adaptive_theta_validation(gpu):
     r3 = torch.ones((17, 17, 17), device=DEV)
     G3 = torch.zeros((17, 17, 17), dtype=torch.uint8, device=DEV)
     with pytest.raises(gpu.EikError):
-        gpu.dd_solve(r3, G3, r3, 1.0 / 16, (2, 2, 2), 4, theta_adaptive=True)
+        gpu.dd_solve(r3, G3, r3, 1.0 / 16, (2, 2, 2), 4, theta_adaptive=True, omega=(0.0, 0.0, 0.0))
+
+
+@pytest.mark.parametrize("n,tiles,c,kmax", [
+    (17, (2, 2, 2), 4, 5),
+    (25, (3, 2, 2), 4, 4),     # c < S on two axes
+])
+def test_dd3_adaptive_theta_fp64_against_oracle(gpu, n, tiles, c, kmax):
+    """The per-node weight of Sec. 4.2 in the 3-D solve: bitwise at the
+    first update, within 1e-11 (the estimate's exp) afterwards."""
+    r, gamma, g, h = _dd3_case(n)
+    kw = dict(theta=0.2, max_coarse_sweeps=8, theta_adaptive=True, theta_cap=1.0, omega=(1.0, 0.5, 0.25))
+    for k in range(1, kmax + 1):
+        u_ref, s_ref, _ = O.dd(r, gamma, g, h, tiles, c, max_iter=k, tol=0.0, **kw)
+        u, st = gpu.dd_solve(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h, tiles, c,
+                             max_iter=k, tol=0.0, **kw)
+        assert st["iters"] == s_ref["iters"] == k
+        a = u.cpu().numpy()
+        if k == 1:
+            np.testing.assert_array_equal(a, u_ref)
+        else:
+            assert _rel(a, u_ref) <= 1e-11, k
 
 
 # The DD workload of the benchmark: 4097^2, 16x16 subdomains, coarse ratio 16,
-# theta 0.2, FP32, in the launch configuration bench.py times.
+# theta 0, FP32, in the launch configuration bench.py times.
 C1_DD = dict(theta=0.0, tol=1e-6, max_coarse_sweeps=8)   # the benchmark's solve
 
 
