@@ -419,3 +419,66 @@ def test_dd3_fp32_converged_against_oracle(gpu):
                          **args)
     assert s_ref["converged"] == 1 and st["converged"] == 1
     assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
+
+
+# --------------------------------------------------------------------------
+# Degenerate and extreme cases of the DD solve (FP64, bitwise against the
+# oracle).
+# --------------------------------------------------------------------------
+def _dd_both(gpu, r, gamma, g, h, tiles, c, k, **kw):
+    kw = dict(dict(theta=0.2, tol=0.0, max_coarse_sweeps=8), **kw)
+    u_ref, s_ref, _ = O.dd(r, gamma, g, h, tiles, c, max_iter=k, **kw)
+    u, st = gpu.dd_solve(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h, tiles, c,
+                         max_iter=k, **kw)
+    assert st["iters"] == s_ref["iters"] and st["error"] == 0
+    return u.cpu().numpy(), u_ref
+
+
+def test_dd_without_sources_stays_infinite(gpu):
+    """Gamma empty: nothing is ever reached; every node stays +inf."""
+    n, h = 33, 1.0 / 32
+    r = I.sin_product((n, n), h, 0.5, 0.25)
+    a, ref = _dd_both(gpu, r, np.zeros((n, n), np.uint8), np.zeros((n, n)), h, (2, 2), 8, 3)
+    assert np.isinf(ref).all()
+    np.testing.assert_array_equal(a, ref)
+
+
+def test_dd_everything_on_gamma_returns_g(gpu):
+    """Gamma = every node: the solution is g, unchanged by every step."""
+    n, h = 33, 1.0 / 32
+    r = I.sin_product((n, n), h, 0.5, 0.25)
+    g = np.random.default_rng(3).uniform(0.0, 1.0, (n, n))
+    a, ref = _dd_both(gpu, r, np.ones((n, n), np.uint8), g, h, (2, 2), 8, 2)
+    np.testing.assert_array_equal(ref, g)
+    np.testing.assert_array_equal(a, g)
+
+
+def test_dd_single_subdomain_is_the_fsm(gpu):
+    """One subdomain: the first fine solve is the plain FSM of the whole grid."""
+    n, h = 65, 1.0 / 64
+    r, gamma, g, h = _dd_case(n, (1, 1), 8)
+    a, ref = _dd_both(gpu, r, gamma, g, h, (1, 1), 8, 0)
+    u_fsm, _ = gpu.fsm(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h)
+    np.testing.assert_array_equal(a, ref)
+    np.testing.assert_array_equal(a, u_fsm.cpu().numpy())
+
+
+def test_dd_largest_subdomain(gpu):
+    """The widest FP64 subdomain whose sweep engine fits in shared memory: 288
+    nodes (9 warps, 212 KB) on a 64 x 288 grid, coarse ratio 7.  A 1024-node
+    subdomain is within the validated range but needs more shared memory than
+    the device has: the call fails with EIK_EUNSUPPORTED before any work."""
+    ny, nx = 64, 288
+    h = 1.0 / (nx - 1)
+    r = I.sin_product((ny, nx), h, 0.5, 0.1)
+    gamma, g = I.point_source((ny, nx), (10, 150))
+    for k in (0, 2):
+        a, ref = _dd_both(gpu, r, gamma, g, h, (1, 1), 7, k)
+        np.testing.assert_array_equal(a, ref)
+    ny, nx = 64, 1024
+    r = torch.ones((ny, nx), dtype=torch.float64, device=DEV)
+    G = torch.zeros((ny, nx), dtype=torch.uint8, device=DEV)
+    G[10, 500] = 1
+    with pytest.raises(gpu.EikError) as e:
+        gpu.dd_solve(r, G, torch.zeros_like(r), 1.0 / 1023, (1, 1), 3, max_iter=1)
+    assert e.value.code == -5
