@@ -15,6 +15,11 @@ Functions (each follows the paper section named in its docstring):
   theta_estimate  per-node weight of Sec. 4.2 (eqs. secthetaest, thetaest)
   model_problem   Sec. 4's model problem, eq. modelprob, with the bounds of
                Theorem 2's proof
+  step4_box    Alg. 5 sweeps on one coarse box (Step 4 of Sec. 3.2)
+  alg4_select  Alg. 4's choice among the copies of one coarse-set node
+  theta_node   Sec. 4.2's weight of one node from its history
+  dd_probe     dd with a per-iteration record of one node
+  dd1          the one-dimensional method of Sec. 3.1 (Steps 1-4)
 """
 from __future__ import annotations
 
@@ -55,6 +60,22 @@ class DDParams(ctypes.Structure):
                 ("theta_cap", ctypes.c_double)]
 
 
+class DD1Params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_long), ("M", ctypes.c_long), ("h", ctypes.c_double), ("theta", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("max_fsm_sweeps", ctypes.c_long),
+                ("max_coarse_sweeps", ctypes.c_long)]
+
+
+class DD1Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("last_delta", ctypes.c_double),
+                ("fsm_sweeps_max", ctypes.c_long), ("coarse_sweeps_max", ctypes.c_long),
+                ("fsm_cap_hits", ctypes.c_long), ("coarse_cap_hits", ctypes.c_long),
+                ("causal_rounds_max", ctypes.c_long), ("fine_updates", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class DDStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("last_delta", ctypes.c_double),
                 ("fsm_sweeps_max", ctypes.c_long), ("coarse_sweeps_max", ctypes.c_long),
@@ -88,6 +109,20 @@ def _load():
             lib.orc_theta_estimate.restype = ctypes.c_double
             lib.orc_theta_estimate.argtypes = [ctypes.POINTER(DDParams), ctypes.c_double, dp, ctypes.c_int,
                                                ctypes.c_double]
+            ip = ctypes.POINTER(ctypes.c_int)
+            lib.orc_step4_box.restype = ctypes.c_long
+            lib.orc_step4_box.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, dp, sp, sp, ip, dp,
+                                          ctypes.c_long, dp, dp, ip]
+            lib.orc_alg4_select.restype = ctypes.c_int
+            lib.orc_alg4_select.argtypes = [ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp, sp, bp, sp]
+            lib.orc_theta_node.restype = ctypes.c_double
+            lib.orc_theta_node.argtypes = [ctypes.POINTER(DDParams), ctypes.c_int] + [ctypes.c_double] * 6
+            lib.orc_dd_probe.restype = ctypes.c_int
+            lib.orc_dd_probe.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, dp, dp, ctypes.POINTER(DDStats),
+                                         ctypes.c_long, dp]
+            lib.orc_dd1.restype = ctypes.c_int
+            lib.orc_dd1.argtypes = [ctypes.POINTER(DD1Params), dp, bp, dp, dp, dp, dp, dp, sp,
+                                    ctypes.POINTER(DD1Stats)]
             lib.orc_adjoint.restype = None
             lib.orc_adjoint.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, dp]
             _lib = lib
@@ -188,6 +223,119 @@ def dd(r, gamma, g, h, tiles, c, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps
     if return_coarse:
         out = out + (U,)
     return out
+
+
+def _params(shape, h, tiles, c, theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps, theta_adaptive, omega,
+            sig_gamma, sig_delta, sig_x0, theta_cap):
+    d, n = _shape_n(shape)
+    t = list(tiles) + [1] * (3 - len(tiles))
+    return DDParams(d, n, float(h), (ctypes.c_int * 3)(*t), int(c), float(theta), int(max_iter), float(tol),
+                    int(max_fsm_sweeps), int(max_coarse_sweeps), 1 if theta_adaptive else 0,
+                    (ctypes.c_double * 3)(*omega), float(sig_gamma), float(sig_delta), float(sig_x0),
+                    float(theta_cap))
+
+
+def dd_probe(r, gamma, g, h, tiles, c, probe, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
+             max_coarse_sweeps=80, theta_adaptive=False, omega=(1.0, 1.0, 1.0), sig_gamma=0.75, sig_delta=0.01,
+             sig_x0=0.9, theta_cap=0.0):
+    """dd (Sec. 3.2) with a record of the node at numpy index ``probe``: returns
+    (u, stats, log) with log[k] = (u^k, C^k = C_H(nbrs U^k), weight used for
+    U^{k+1}, U^k) at that node, NaN where iteration k did not compute it."""
+    lib = _load()
+    r, gamma, g = _prep(r, gamma, g)
+    p = _params(r.shape, h, tiles, c, theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps, theta_adaptive,
+                omega, sig_gamma, sig_delta, sig_x0, theta_cap)
+    u = np.empty_like(r)
+    U = np.empty_like(r)
+    dlog = np.empty(max_iter + 1, dtype=np.float64)
+    plog = np.empty((max_iter + 1, 4), dtype=np.float64)
+    st = DDStats()
+    flat = int(np.ravel_multi_index(probe, r.shape))
+    rc = lib.orc_dd_probe(ctypes.byref(p), _dp(r), _bp(gamma), _dp(g), _dp(u), _dp(U), _dp(dlog), ctypes.byref(st),
+                          flat, _dp(plog))
+    if rc != 0:
+        raise ValueError("oracle dd_probe: invalid parameters")
+    return u, st.as_dict(), plog
+
+
+def step4_box(H, r, fixed, g, Uk, uk, wk, Wk, axes, theta, max_sweeps=80):
+    """Alg. 5 sweeps on one coarse box (Step 4 of Sec. 3.2).  Arrays are numpy
+    arrays of the box shape ((y, x) or (z, y, x)); wk, Wk carry a trailing axis
+    of d wind components in (x, y[, z]) order; axes[...] has bit k set when the
+    node lies on a coarse line of axis k; theta is a scalar or per node.
+    Returns (U, C_H(nbrs U^k), sweeps, capped)."""
+    lib = _load()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    shape = r.shape
+    d, n = _shape_n(shape)
+    fixed = np.ascontiguousarray(fixed, dtype=np.uint8)
+    g = np.ascontiguousarray(np.broadcast_to(g, shape), dtype=np.float64)
+    Uk = np.ascontiguousarray(Uk, dtype=np.float64)
+    uk = np.ascontiguousarray(uk, dtype=np.float64)
+
+    def winds(w):
+        out = np.zeros(shape + (3,), dtype=np.int8)
+        out[..., :d] = np.asarray(w, dtype=np.int8)
+        return out
+
+    wk3, Wk3 = winds(wk), winds(Wk)
+    ax = np.ascontiguousarray(np.broadcast_to(axes, shape), dtype=np.int32)
+    th = np.ascontiguousarray(np.broadcast_to(theta, shape), dtype=np.float64)
+    U = np.empty(shape)
+    C = np.empty(shape)
+    capped = ctypes.c_int(0)
+    s = lib.orc_step4_box(d, n, float(H), _dp(r), _bp(fixed), _dp(g), _dp(Uk), _dp(uk), _sp(wk3), _sp(Wk3),
+                          ax.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(th), int(max_sweeps), _dp(U), _dp(C),
+                          ctypes.byref(capped))
+    return U, C, int(s), bool(capped.value)
+
+
+def alg4_select(B, nc, u, w, echo, W, d=2):
+    """Alg. 4's choice at one coarse-set node: index of the chosen copy."""
+    lib = _load()
+    ncopies = len(u)
+    nca = (ctypes.c_int * 3)(*(list(nc) + [1] * (3 - len(nc))))
+    ua = np.ascontiguousarray(u, dtype=np.float64)
+    wa = np.zeros((ncopies, 3), dtype=np.int8)
+    wa[:, :d] = np.asarray(w, dtype=np.int8)
+    ea = np.ascontiguousarray(echo, dtype=np.uint8)
+    Wa = np.zeros(3, dtype=np.int8)
+    Wa[:d] = np.asarray(W, dtype=np.int8)
+    return lib.orc_alg4_select(d, int(B), nca, ncopies, _dp(ua), _sp(wa), _bp(ea), _sp(Wa))
+
+
+def theta_node(nhist, Ck, C1, C2, C3, uk, uprev, theta=0.2, omega=(1.0, 1.0, 1.0), sig_gamma=0.75, sig_delta=0.01,
+               sig_x0=0.9, theta_cap=0.0, adaptive=True):
+    """Sec. 4.2's weight of one node from its history (C^k .. C^{k-3}, u^k, u^{k-1})."""
+    lib = _load()
+    p = _params((1, 1), 1.0, (1, 1), 1, theta, 0, 0.0, 1, 1, adaptive, omega, sig_gamma, sig_delta, sig_x0,
+                theta_cap)
+    return lib.orc_theta_node(ctypes.byref(p), int(nhist), float(Ck), float(C1), float(C2), float(C3), float(uk),
+                              float(uprev))
+
+
+def dd1(r, gamma, g, h, N, M, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000, max_coarse_sweeps=1000):
+    """The one-dimensional method of Sec. 3.1 on a fine grid of N*M+1 nodes
+    (coarse node every M).  Returns (u, stats, logs) with logs a dict of
+    (max_iter+1, N+1) arrays: U (U^k), u (u^k), W (W^k) and Upre (Step 4's
+    result of iteration k before the causal sweep); unused rows are NaN / 0."""
+    lib = _load()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    gamma = np.ascontiguousarray(gamma, dtype=np.uint8)
+    g = np.ascontiguousarray(np.broadcast_to(g, r.shape), dtype=np.float64)
+    assert r.shape == (N * M + 1,)
+    p = DD1Params(int(N), int(M), float(h), float(theta), int(max_iter), float(tol), int(max_fsm_sweeps),
+                  int(max_coarse_sweeps))
+    u = np.empty_like(r)
+    logs = {k: np.full((max_iter + 1, N + 1), np.nan) for k in ("U", "u", "Upre")}
+    Wl = np.zeros((max_iter + 1, N + 1), dtype=np.int8)
+    st = DD1Stats()
+    rc = lib.orc_dd1(ctypes.byref(p), _dp(r), _bp(gamma), _dp(g), _dp(u), _dp(logs["U"]), _dp(logs["u"]),
+                     _dp(logs["Upre"]), _sp(Wl), ctypes.byref(st))
+    if rc != 0:
+        raise ValueError("oracle dd1: invalid parameters")
+    logs["W"] = Wl
+    return u, st.as_dict(), logs
 
 
 def theta_estimate(du, dC, omega=(1.0, 1.0, 1.0), sig_gamma=0.75, sig_delta=0.01, sig_x0=0.9, theta_cap=0.0,

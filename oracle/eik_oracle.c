@@ -524,35 +524,132 @@ double orc_theta_estimate(const orc_dd_params *p, double du, const double *dC, i
     return v > 0.0 ? v : 0.0;
 }
 
-static double theta_node(const theta_ctx *T, long f, double uk_f, double Ck_f)
+/* The weight of one node from its history: Ck = C^k, C1..C3 = C^{k-1..k-3}
+ * (only the first nhist are read), uk = u^k, uprev = u^{k-1}.  The s-th term
+ * of the mean is C^{k-s} - C^{k-1-s}. */
+double orc_theta_node(const orc_dd_params *p, int nhist, double Ck, double C1, double C2, double C3, double uk,
+                      double uprev)
 {
-    const orc_dd_params *p = T->p;
-    const double *Cs[4];
-    double dC[3];
+    double Cs[4], dC[3];
     int s, n;
-    if (!p->theta_adaptive || T->nhist < 1) return p->theta;
-    Cs[1] = T->C1;
-    Cs[2] = T->C2;
-    Cs[3] = T->C3;
-    n = T->nhist < 3 ? T->nhist : 3;
-    for (s = 0; s < n; ++s) dC[s] = ((s == 0) ? Ck_f : Cs[s][f]) - Cs[s + 1][f];
-    return orc_theta_estimate(p, uk_f - T->uprev[f], dC, n, p->theta);
+    if (!p->theta_adaptive || nhist < 1) return p->theta;
+    Cs[0] = Ck;
+    Cs[1] = C1;
+    Cs[2] = C2;
+    Cs[3] = C3;
+    n = nhist < 3 ? nhist : 3;
+    for (s = 0; s < n; ++s) dC[s] = Cs[s] - Cs[s + 1];
+    return orc_theta_estimate(p, uk - uprev, dC, n, p->theta);
 }
 
-/* Step 4 on one shifted grid: Alg. 5.  Uk = U^k (for C_H(nbrs U^k)), uk/wk the
- * Alg. 4 output, Wk = W^k.  Writes the swept U (W is set to w^k by the caller)
- * and C_H(nbrs U^k) at the grid's nodes into Cout (full grid, may be NULL).
- * The weight of a node is theta_node(T, ...) (T may be NULL: constant theta). */
+static double theta_node(const theta_ctx *T, long f, double uk_f, double Ck_f)
+{
+    if (!T->p->theta_adaptive || T->nhist < 1) return T->p->theta;
+    return orc_theta_node(T->p, T->nhist, Ck_f, T->C1[f], T->nhist > 1 ? T->C2[f] : 0.0,
+                          T->nhist > 2 ? T->C3[f] : 0.0, uk_f, T->uprev[f]);
+}
+
+/* C_H(nbrs^H(U^k)) at every node of a box (Sec. 3.2, the coarse solver
+ * applied to the previous iterate; Step 4's last term). */
+static void coarse_solver_prev(int d, const long *m, double H, const double *r, const double *Uk, double *Cold)
+{
+    long x, y, z;
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long l = lidx(m, x, y, z);
+                double vm[3], vp[3];
+                signed char w[3];
+                nbrs(d, m, Uk, x, y, z, vm, vp);
+                Cold[l] = orc_local_solve(d, vm, vp, r[l] * H, w);
+            }
+}
+
+/* Alg. 5 sweeps on one box (the U update of Step 4, Sec. 3.2).  U is
+ * initialised as in Sec. 1.1 (fixed nodes at g, the rest +inf) and swept in
+ * the 2^d orderings; at a free node with U~, W~ from the current neighbours
+ * (Alg. 1), the weighted update u^k + theta (U~ - C_H(U^k)) is taken when on
+ * every coarse-line axis of the node (bit k of axes) w^k, W^k and W~ all point
+ * the same way or are zero, otherwise u^k.  Stops after a sweep that changes
+ * nothing or max_sweeps sweeps (*capped = 1). */
+static long alg5_sweeps(int d, const long *m, double H, const double *r, const unsigned char *fixed,
+                        const double *g, const double *uk, const signed char *wk, const signed char *Wk,
+                        const int *axes, const double *Cold, const double *theta, long max_sweeps, double *U,
+                        int *capped)
+{
+    long s = 0, x, y, z, M = m[0] * m[1] * m[2], l;
+    int nq = 1 << d;
+    *capped = 0;
+    /* "Initialize U as described in Sec. 1.1" */
+    for (l = 0; l < M; ++l) U[l] = fixed[l] ? g[l] : INF;
+    for (;;) {
+        int changed = 0, sg[3];
+        if (s >= max_sweeps) {
+            *capped = 1;
+            break;
+        }
+        ordering(d, (int)(s % nq), sg);
+        for (x = start_of(m[0], sg[0]); x >= 0 && x < m[0]; x += sg[0])
+            for (y = start_of(m[1], sg[1]); y >= 0 && y < m[1]; y += sg[1])
+                for (z = start_of(m[2], sg[2]); z >= 0 && z < m[2]; z += sg[2]) {
+                    double vm[3], vp[3], Ut, Unew;
+                    signed char Wt[3];
+                    int pass, k;
+                    l = lidx(m, x, y, z);
+                    if (fixed[l]) continue;
+                    nbrs(d, m, U, x, y, z, vm, vp);
+                    Ut = orc_local_solve(d, vm, vp, r[l] * H, Wt);
+                    /* Alg. 5 agreement test, per coarse-line axis: the fine wind
+                     * w^k, the coarse wind W^k and the current wind W~ all point
+                     * the same way (or are zero) along that axis. */
+                    pass = (Ut < INF) && (Cold[l] < INF);
+                    for (k = 0; k < d && pass; ++k) {
+                        int a = wk[3 * l + k], b = Wk[3 * l + k], c = Wt[k];
+                        if (!(axes[l] & (1 << k))) continue;
+                        if (!((a <= 0 && b <= 0 && c <= 0) || (a >= 0 && b >= 0 && c >= 0))) pass = 0;
+                    }
+                    if (pass)
+                        Unew = uk[l] + theta[l] * (Ut - Cold[l]);
+                    else
+                        Unew = uk[l];
+                    if (!(Unew == U[l])) changed = 1;
+                    U[l] = Unew;
+                }
+        ++s;
+        if (!changed) break;
+    }
+    return s;
+}
+
+long orc_step4_box(int d, const long *n, double H, const double *r, const unsigned char *fixed, const double *g,
+                   const double *Uk, const double *uk, const signed char *wk, const signed char *Wk,
+                   const int *axes, const double *theta, long max_sweeps, double *U, double *Cold, int *capped)
+{
+    long m[3] = {n[0], d > 1 ? n[1] : 1, d > 2 ? n[2] : 1};
+    long M = m[0] * m[1] * m[2];
+    double *C = Cold ? Cold : malloc(sizeof(double) * (size_t)M);
+    long s;
+    coarse_solver_prev(d, m, H, r, Uk, C);
+    s = alg5_sweeps(d, m, H, r, fixed, g, uk, wk, Wk, axes, C, theta, max_sweeps, U, capped);
+    if (!Cold) free(C);
+    return s;
+}
+
+/* Step 4 on one shifted grid: gathers the grid's nodes into a dense box and
+ * runs Alg. 5 there.  Uk = U^k (for C_H(nbrs U^k)), uk/wk the Alg. 4 output,
+ * Wk = W^k.  Writes the swept U (W is set to w^k by the caller) and
+ * C_H(nbrs U^k) at the grid's nodes into Cout (full grid, may be NULL).  The
+ * weight of a node is theta_node(T, ...) (T may be NULL: constant theta); it
+ * is also written to theta_out (full grid, may be NULL). */
 static long step4_grid(const geom_t *G, const long *o, double H, double theta, const double *r,
                        const unsigned char *gamma, const double *g, const double *Uk, const double *uk,
                        const signed char *wk, const signed char *Wk, double *U, long max_sweeps, long *caps,
-                       const theta_ctx *T, double *Cout)
+                       const theta_ctx *T, double *Cout, double *theta_out)
 {
     long m[3], M, s = 0, x, y, z;
-    int nq = 1 << G->d, d = G->d;
-    double *Ul, *Ukl, *Cold, *ukl, *rl, *thl;
+    double *Ul, *Ukl, *Cold, *ukl, *rl, *thl, *gl;
     unsigned char *fl;
-    int *Al;
+    int *Al, capped;
     long *fidx;
     signed char *wkl, *Wkl;
     grid_box(G, o, m);
@@ -561,6 +658,7 @@ static long step4_grid(const geom_t *G, const long *o, double H, double theta, c
     Ukl = malloc(sizeof(double) * (size_t)M);
     Cold = malloc(sizeof(double) * (size_t)M);
     thl = malloc(sizeof(double) * (size_t)M);
+    gl = malloc(sizeof(double) * (size_t)M);
     fidx = malloc(sizeof(long) * (size_t)M);
     ukl = malloc(sizeof(double) * (size_t)M);
     rl = malloc(sizeof(double) * (size_t)M);
@@ -577,6 +675,7 @@ static long step4_grid(const geom_t *G, const long *o, double H, double theta, c
                 rl[l] = r[f];
                 fidx[l] = f;
                 fl[l] = gamma[f] ? 1 : 0;
+                gl[l] = g[f];
                 Ukl[l] = Uk[f];
                 ukl[l] = uk[f];
                 Al[l] = coarse_axes(G, xf);
@@ -584,62 +683,26 @@ static long step4_grid(const geom_t *G, const long *o, double H, double theta, c
                     wkl[3 * l + k] = wk[3 * f + k];
                     Wkl[3 * l + k] = Wk[3 * f + k];
                 }
-                /* "Initialize U as described in Sec. 1.1" */
-                Ul[l] = gamma[f] ? g[f] : INF;
             }
-    /* C_H(nbrs^H(U^k)) at every node, from the previous iterate. */
+    /* C_H(nbrs^H(U^k)) at every node, from the previous iterate, then the
+     * weight of every node (constant, or Sec. 4.2's estimate). */
+    coarse_solver_prev(G->d, m, H, rl, Ukl, Cold);
     for (z = 0; z < m[2]; ++z)
         for (y = 0; y < m[1]; ++y)
             for (x = 0; x < m[0]; ++x) {
                 long l = lidx(m, x, y, z);
-                double vm[3], vp[3];
-                signed char w[3];
-                nbrs(d, m, Ukl, x, y, z, vm, vp);
-                Cold[l] = orc_local_solve(d, vm, vp, rl[l] * H, w);
                 thl[l] = T ? theta_node(T, fidx[l], ukl[l], Cold[l]) : theta;
                 if (Cout) Cout[fidx[l]] = Cold[l];
+                if (theta_out) theta_out[fidx[l]] = thl[l];
             }
-    for (;;) {
-        int changed = 0, sg[3];
-        if (s >= max_sweeps) {
-            ++*caps;
-            break;
-        }
-        ordering(d, (int)(s % nq), sg);
-        for (x = start_of(m[0], sg[0]); x >= 0 && x < m[0]; x += sg[0])
-            for (y = start_of(m[1], sg[1]); y >= 0 && y < m[1]; y += sg[1])
-                for (z = start_of(m[2], sg[2]); z >= 0 && z < m[2]; z += sg[2]) {
-                    long l = lidx(m, x, y, z);
-                    double vm[3], vp[3], Ut, Unew;
-                    signed char Wt[3];
-                    int pass, k;
-                    if (fl[l]) continue;
-                    nbrs(d, m, Ul, x, y, z, vm, vp);
-                    Ut = orc_local_solve(d, vm, vp, rl[l] * H, Wt);
-                    /* Alg. 5 agreement test, per coarse-line axis: the fine wind
-                     * w^k, the coarse wind W^k and the current wind W~ all point
-                     * the same way (or are zero) along that axis. */
-                    pass = (Ut < INF) && (Cold[l] < INF);
-                    for (k = 0; k < d && pass; ++k) {
-                        int a = wkl[3 * l + k], b = Wkl[3 * l + k], c = Wt[k];
-                        if (!(Al[l] & (1 << k))) continue;
-                        if (!((a <= 0 && b <= 0 && c <= 0) || (a >= 0 && b >= 0 && c >= 0))) pass = 0;
-                    }
-                    if (pass)
-                        Unew = ukl[l] + thl[l] * (Ut - Cold[l]);
-                    else
-                        Unew = ukl[l];
-                    if (!(Unew == Ul[l])) changed = 1;
-                    Ul[l] = Unew;
-                }
-        ++s;
-        if (!changed) break;
-    }
+    s = alg5_sweeps(G->d, m, H, rl, fl, gl, ukl, wkl, Wkl, Al, Cold, thl, max_sweeps, Ul, &capped);
+    if (capped) ++*caps;
     grid_scatter_d(G, o, m, Ul, U);
     free(Ul);
     free(Ukl);
     free(Cold);
     free(thl);
+    free(gl);
     free(fidx);
     free(ukl);
     free(rl);
@@ -720,6 +783,66 @@ static long step23_tile(const geom_t *G, const int *t, double h, const double *r
     return s;
 }
 
+/* Alg. 4's choice at one coarse-set node (Sec. 3.2).  The node lies on the
+ * interfaces of the axes in B (bit k); nc[k] = 2 copies along such an axis
+ * (minus-side subdomain first), 1 otherwise; the copies are enumerated with
+ * axis 0 fastest, i.e. in ascending linear subdomain index.  Copy q has value
+ * u[q], wind w[3q..3q+2] and echo flag echo[q]; W is the coarse wind W^k.
+ * Per interface axis: when every fine wind and W^k point toward -axis (or
+ * are zero) the plus-side copy is taken (Alg. 4's first branch), when they
+ * all point toward +axis the minus-side copy; if some axis has neither, the
+ * minimum of the fine solutions (echoes only when every copy is one; ties to
+ * the lowest index).  Returns the index of the chosen copy. */
+int orc_alg4_select(int d, int B, const int *nc, int ncopies, const double *u, const signed char *w,
+                    const unsigned char *echo, const signed char *W)
+{
+    int k, q, ok = 1, sel[3] = {0, 0, 0}, best;
+    if (!B) return 0;
+    for (k = 0; k < d && ok; ++k) {
+        int allneg = 1, allpos = 1;
+        if (!(B & (1 << k))) continue;
+        if (W[k] > 0) allneg = 0;
+        if (W[k] < 0) allpos = 0;
+        for (q = 0; q < ncopies; ++q) {
+            int wv = w[3 * q + k];
+            if (wv > 0) allneg = 0;
+            if (wv < 0) allpos = 0;
+        }
+        /* Alg. 4: first branch (wind toward -axis: take the plus-side
+         * copy) wins when both hold; then the minus-side copy. */
+        if (allneg)
+            sel[k] = 1;
+        else if (allpos)
+            sel[k] = 0;
+        else
+            ok = 0;
+    }
+    if (ok) {
+        /* index of the selected copy in the enumeration */
+        int stride = 1;
+        best = 0;
+        for (k = 0; k < 3; ++k) {
+            best += sel[k] * stride;
+            stride *= nc[k];
+        }
+        return best;
+    }
+    /* otherwise the minimum of the fine solutions: copies that only echo
+     * their Step 2 boundary value are not candidates unless every copy is
+     * one; ties keep the lowest subdomain index */
+    {
+        int computed = 0;
+        for (q = 0; q < ncopies; ++q)
+            if (!echo[q]) computed = 1;
+        best = -1;
+        for (q = 0; q < ncopies; ++q) {
+            if (computed && echo[q]) continue;
+            if (best < 0 || u[q] < u[best]) best = q;
+        }
+    }
+    return best;
+}
+
 /* Alg. 4 at every coarse-set node: choose u^k, w^k among the subdomain copies. */
 static void alg4(const geom_t *G, double **tu, signed char **tw, unsigned char **te, const signed char *W, double *uk,
                  signed char *wk)
@@ -732,8 +855,11 @@ static void alg4(const geom_t *G, double **tu, signed char **tw, unsigned char *
         long x[3];
         long cand[3][2];
         int nc[3], B = 0;
-        int A, q, ncopies, best, sel[3], ok;
+        int A, q, ncopies, best;
         long cidx[8], lidxs[8];
+        double cu[8];
+        signed char cw[24];
+        unsigned char ce[8];
         coords(G, i, x);
         A = coarse_axes(G, x);
         if (!A) continue;
@@ -770,54 +896,14 @@ static void alg4(const geom_t *G, double **tu, signed char **tw, unsigned char *
                         ++ncopies;
                     }
         }
-        best = 0;
-        ok = 1;
-        for (k = 0; k < 3; ++k) sel[k] = 0;
-        if (B) {
-            for (k = 0; k < G->d && ok; ++k) {
-                int allneg = 1, allpos = 1;
-                if (!(B & (1 << k))) continue;
-                if (W[3 * i + k] > 0) allneg = 0;
-                if (W[3 * i + k] < 0) allpos = 0;
-                for (q = 0; q < ncopies; ++q) {
-                    int wv = tw[cidx[q]][3 * lidxs[q] + k];
-                    if (wv > 0) allneg = 0;
-                    if (wv < 0) allpos = 0;
-                }
-                /* Alg. 4: first branch (wind toward -axis: take the plus-side
-                 * copy) wins when both hold; then the minus-side copy. */
-                if (allneg)
-                    sel[k] = 1;
-                else if (allpos)
-                    sel[k] = 0;
-                else
-                    ok = 0;
-            }
-            if (ok) {
-                /* index of the selected copy in the enumeration */
-                int stride = 1;
-                best = 0;
-                for (k = 0; k < 3; ++k) {
-                    best += sel[k] * stride;
-                    stride *= nc[k];
-                }
-            } else {
-                /* otherwise the minimum of the fine solutions: copies that
-                 * only echo their Step 2 boundary value are not candidates
-                 * unless every copy is one; ties keep the lowest subdomain
-                 * index */
-                int computed = 0;
-                for (q = 0; q < ncopies; ++q)
-                    if (!te[cidx[q]][lidxs[q]]) computed = 1;
-                best = -1;
-                for (q = 0; q < ncopies; ++q) {
-                    if (computed && te[cidx[q]][lidxs[q]]) continue;
-                    if (best < 0 || tu[cidx[q]][lidxs[q]] < tu[cidx[best]][lidxs[best]]) best = q;
-                }
-            }
+        for (q = 0; q < ncopies; ++q) {
+            cu[q] = tu[cidx[q]][lidxs[q]];
+            ce[q] = te[cidx[q]][lidxs[q]];
+            for (k = 0; k < 3; ++k) cw[3 * q + k] = tw[cidx[q]][3 * lidxs[q] + k];
         }
-        uk[i] = tu[cidx[best]][lidxs[best]];
-        for (k = 0; k < 3; ++k) wk[3 * i + k] = tw[cidx[best]][3 * lidxs[best] + k];
+        best = orc_alg4_select(G->d, B, nc, ncopies, cu, cw, ce, W + 3 * i);
+        uk[i] = cu[best];
+        for (k = 0; k < 3; ++k) wk[3 * i + k] = cw[3 * best + k];
     }
 }
 
@@ -837,8 +923,9 @@ static double coarse_delta(const geom_t *G, const double *U1, const double *U0)
     return dmax;
 }
 
-int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
-           double *u_out, double *U_out, double *delta_log, orc_dd_stats *st)
+static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
+                      double *u_out, double *U_out, double *delta_log, orc_dd_stats *st, long probe,
+                      double *probe_log)
 {
     geom_t G;
     long i, ntiles;
@@ -850,6 +937,7 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     long tilenodes;
     orc_dd_stats S0;
     theta_ctx tctx;
+    double *thfull = NULL;
     memset(&S0, 0, sizeof(S0));
     if (p->d < 2 || p->d > 3 || p->c < 1) return -1;
     memset(&G, 0, sizeof(G));
@@ -873,6 +961,7 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     ntiles = (long)G.T[0] * G.T[1] * G.T[2];
     tilenodes = 1;
     for (k = 0; k < p->d; ++k) tilenodes *= G.S[k] + 1;
+    if (probe_log && (probe < 0 || probe >= G.N)) return -1;
 
     U = malloc(sizeof(double) * (size_t)G.N);
     Uprev = malloc(sizeof(double) * (size_t)G.N);
@@ -890,6 +979,11 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
         te[i] = malloc((size_t)tilenodes);
     }
     for (i = 0; i < G.N; ++i) U[i] = uk[i] = NAN;
+    if (probe_log) {
+        for (k = 0; k < 4 * (p->max_iter + 1); ++k) probe_log[k] = NAN;
+        thfull = malloc(sizeof(double) * (size_t)G.N);
+        for (i = 0; i < G.N; ++i) thfull[i] = NAN;
+    }
 
     /* Step 1: every shifted coarse grid, independently; then the causal sweep. */
     {
@@ -930,6 +1024,10 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
                 }
         /* Alg. 4 */
         alg4(&G, tu, tw, te, W, uk, wk);
+        if (thfull) {
+            probe_log[4 * it + 0] = uk[probe];
+            probe_log[4 * it + 3] = U[probe];
+        }
         S0.iters = it;
         if (it == p->max_iter) break;
         if (it >= 1 && delta < p->tol) {
@@ -953,7 +1051,7 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
                 long s;
                 first = 0;
                 s = step4_grid(&G, o, H, p->theta, r, gamma, g, Uprev, uk, wk, W, Unew, p->max_coarse_sweeps,
-                               &S0.coarse_cap_hits, &tctx, Chist[it % 4]);
+                               &S0.coarse_cap_hits, &tctx, Chist[it % 4], thfull);
                 if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
                 {
                     long m[3];
@@ -963,6 +1061,10 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
             }
             memcpy(U, Unew, sizeof(double) * (size_t)G.N);
             free(Unew);
+        }
+        if (thfull) {
+            probe_log[4 * it + 1] = Chist[it % 4][probe];
+            probe_log[4 * it + 2] = thfull[probe];
         }
         for (i = 0; i < G.N; ++i) {
             long x[3];
@@ -1019,6 +1121,268 @@ int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, 
     free(uk);
     free(W);
     free(wk);
+    free(thfull);
+    return 0;
+}
+
+int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
+           double *u_out, double *U_out, double *delta_log, orc_dd_stats *st)
+{
+    return dd_iterate(p, r, gamma, g, u_out, U_out, delta_log, st, -1, NULL);
+}
+
+int orc_dd_probe(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
+                 double *u_out, double *U_out, double *delta_log, orc_dd_stats *st, long probe_node,
+                 double *probe_log)
+{
+    return dd_iterate(p, r, gamma, g, u_out, U_out, delta_log, st, probe_node, probe_log);
+}
+
+/* ------------------------------------------------------------------------- */
+/* The one-dimensional method, Sec. 3.1 (Steps 1-4).                           */
+/* Fine grid x_j = j h, j = 0..N M; coarse grid X_i = i H = x_{iM}; subinterval */
+/* i holds fine nodes iM..iM+M.  Readings shared with the 2-D method: winds     */
+/* are directions of travel (+1 when the left neighbour gives the minimum; the  */
+/* sign printed in Step 4 for W~ is read as flipped, as in 2-D); ties go to the */
+/* right neighbour (-1); inflow boundary nodes start at U and are swept, and    */
+/* one that keeps U echoes the coarse wind and is no candidate of the minimum   */
+/* unless both copies are echoes; the weighted update is evaluated as           */
+/* u^k + theta (U~ - C_H(U^k)), and u^k when U~ or C_H(U^k) is +inf; the       */
+/* causal sweep is repeated until nothing changes.  Step 1 has no causal sweep  */
+/* (the 2-D text adds one there); the Step 3 choice compares the two fine      */
+/* winds only, as printed (no W^k in the 1-D rule); the Step 4 test is the      */
+/* printed equality W^k = w^k = W~.                                             */
+/* ------------------------------------------------------------------------- */
+
+/* C_H(U_{i-1}, U_{i+1}) of eq. 1dgod at coarse node i (+inf outside), with the
+ * wind of the neighbour used. */
+static double ch1(const double *U, long i, long N, double rH, int *w)
+{
+    double a = (i > 0) ? U[i - 1] : INF, b = (i < N) ? U[i + 1] : INF, v;
+    if (a < b) {
+        v = a + rH;
+        *w = +1;
+    } else {
+        v = b + rH;
+        *w = -1;
+    }
+    if (!(v < INF)) *w = 0;
+    return v;
+}
+
+int orc_dd1(const orc_dd1_params *p, const double *r, const unsigned char *gamma, const double *g, double *u_out,
+            double *U_log, double *u_log, double *Upre_log, signed char *W_log, orc_dd1_stats *st)
+{
+    const long N = p->N, M = p->M, nf = p->N * p->M + 1;
+    const double H = (double)p->M * p->h;
+    long i, j, k, sub;
+    double *U, *Uprev, *Unew, *uk, *Cold, **tu, delta = INF;
+    signed char *W, *wk, **tw;
+    unsigned char *cfix, **te;
+    orc_dd1_stats S0;
+    if (N < 1 || M < 1 || p->max_iter < 0 || !(p->h > 0.0)) return -1;
+    memset(&S0, 0, sizeof(S0));
+    U = malloc(sizeof(double) * (size_t)(N + 1));
+    Uprev = malloc(sizeof(double) * (size_t)(N + 1));
+    Unew = malloc(sizeof(double) * (size_t)(N + 1));
+    uk = malloc(sizeof(double) * (size_t)(N + 1));
+    Cold = malloc(sizeof(double) * (size_t)(N + 1));
+    W = calloc((size_t)(N + 1), 1);
+    wk = calloc((size_t)(N + 1), 1);
+    cfix = malloc((size_t)(N + 1));
+    tu = malloc(sizeof(double *) * (size_t)N);
+    tw = malloc(sizeof(signed char *) * (size_t)N);
+    te = malloc(sizeof(unsigned char *) * (size_t)N);
+    for (sub = 0; sub < N; ++sub) {
+        tu[sub] = malloc(sizeof(double) * (size_t)(M + 1));
+        tw[sub] = malloc((size_t)(3 * (M + 1)));
+        te[sub] = malloc((size_t)(M + 1));
+    }
+    for (i = 0; i <= N; ++i) cfix[i] = gamma[i * M] ? 1 : 0;
+
+    /* Step 1: FSM on the coarse grid (spacing H, r sampled at X_i), winds. */
+    {
+        long mc[3] = {N + 1, 1, 1};
+        double *rc = malloc(sizeof(double) * (size_t)(N + 1));
+        signed char *wc = calloc((size_t)(3 * (N + 1)), 1);
+        int conv;
+        long s;
+        for (i = 0; i <= N; ++i) {
+            rc[i] = r[i * M];
+            U[i] = cfix[i] ? g[i * M] : INF;
+        }
+        s = fsm_local(1, mc, H, rc, cfix, U, p->max_coarse_sweeps, &conv);
+        if (!conv) ++S0.coarse_cap_hits;
+        if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
+        winds_local(1, mc, H, rc, cfix, U, wc);
+        for (i = 0; i <= N; ++i) W[i] = cfix[i] ? 0 : wc[3 * i];
+        free(rc);
+        free(wc);
+    }
+
+    for (k = 0;; ++k) {
+        if (U_log)
+            for (i = 0; i <= N; ++i) U_log[k * (N + 1) + i] = U[i];
+        if (W_log)
+            for (i = 0; i <= N; ++i) W_log[k * (N + 1) + i] = W[i];
+        /* Steps 2 + 3: every subinterval on its own. */
+        for (sub = 0; sub < N; ++sub) {
+            long m[3] = {M + 1, 1, 1};
+            double *rl = malloc(sizeof(double) * (size_t)(M + 1));
+            double *u0 = malloc(sizeof(double) * (size_t)(M + 1));
+            unsigned char *fl = malloc((size_t)(M + 1)), *in = malloc((size_t)(M + 1));
+            int conv;
+            long s;
+            for (j = 0; j <= M; ++j) {
+                long f = sub * M + j;
+                rl[j] = r[f];
+                fl[j] = gamma[f] ? 1 : 0;
+                in[j] = 0;
+                tw[sub][3 * j] = tw[sub][3 * j + 1] = tw[sub][3 * j + 2] = 0;
+                if (fl[j]) {
+                    tu[sub][j] = g[f];
+                    continue;
+                }
+                /* Step 2: U where the characteristic arrives into the
+                 * subinterval (W = +1 at its left end, W = -1 at its right
+                 * end), +inf otherwise. */
+                if (j == 0 && W[sub] > 0) in[j] = 1;
+                if (j == M && W[sub + 1] < 0) in[j] = 1;
+                tu[sub][j] = in[j] ? U[j == 0 ? sub : sub + 1] : INF;
+            }
+            memcpy(u0, tu[sub], sizeof(double) * (size_t)(M + 1));
+            s = fsm_local(1, m, p->h, rl, fl, tu[sub], p->max_fsm_sweeps, &conv);
+            if (!conv) ++S0.fsm_cap_hits;
+            if (s > S0.fsm_sweeps_max) S0.fsm_sweeps_max = s;
+            S0.fine_updates += (long long)s * (M + 1);
+            winds_local(1, m, p->h, rl, fl, tu[sub], tw[sub]);
+            for (j = 0; j <= M; ++j) {
+                te[sub][j] = (unsigned char)(in[j] && tu[sub][j] == u0[j]);
+                if (te[sub][j]) tw[sub][3 * j] = W[j == 0 ? sub : sub + 1];
+            }
+            free(rl);
+            free(u0);
+            free(fl);
+            free(in);
+        }
+        /* Step 3's choice of u^k_i, w^k_i between the two fine values. */
+        for (i = 0; i <= N; ++i) {
+            if (i == 0) {
+                uk[i] = tu[0][0];
+                wk[i] = tw[0][0];
+            } else if (i == N) {
+                uk[i] = tu[N - 1][M];
+                wk[i] = tw[N - 1][3 * M];
+            } else {
+                double uL = tu[i - 1][M], uR = tu[i][0];
+                int wL = tw[i - 1][3 * M], wR = tw[i][0];
+                int eL = te[i - 1][M], eR = te[i][0], takeL;
+                if (wL == 1 && wR == 1)
+                    takeL = 1; /* wind from left to right */
+                else if (wL == -1 && wR == -1)
+                    takeL = 0; /* wind from right to left */
+                else if (eL != eR)
+                    takeL = eR; /* the computed value of the two */
+                else
+                    takeL = !(uR < uL); /* minimum, tie to the left copy */
+                uk[i] = takeL ? uL : uR;
+                wk[i] = (signed char)(takeL ? wL : wR);
+            }
+        }
+        if (u_log)
+            for (i = 0; i <= N; ++i) u_log[k * (N + 1) + i] = uk[i];
+        S0.iters = (int)k;
+        if (k == p->max_iter) break;
+        if (k >= 1 && delta < p->tol) {
+            S0.converged = 1;
+            break;
+        }
+        /* Step 4: weighted coarse sweeps. */
+        memcpy(Uprev, U, sizeof(double) * (size_t)(N + 1));
+        for (i = 0; i <= N; ++i) {
+            int wd;
+            Cold[i] = ch1(Uprev, i, N, r[i * M] * H, &wd);
+            Unew[i] = cfix[i] ? g[i * M] : INF; /* initialise as in FSM */
+        }
+        {
+            long s = 0;
+            for (;;) {
+                int changed = 0;
+                long step = (s % 2 == 0) ? -1 : +1, i0 = (step > 0) ? 0 : N;
+                if (s >= p->max_coarse_sweeps) {
+                    ++S0.coarse_cap_hits;
+                    break;
+                }
+                for (i = i0; i >= 0 && i <= N; i += step) {
+                    int Wt;
+                    double Ut, v;
+                    if (cfix[i]) continue;
+                    Ut = ch1(Unew, i, N, r[i * M] * H, &Wt);
+                    if (Ut < INF && Cold[i] < INF && W[i] == wk[i] && wk[i] == Wt)
+                        v = uk[i] + p->theta * (Ut - Cold[i]);
+                    else
+                        v = uk[i];
+                    if (!(v == Unew[i])) changed = 1;
+                    Unew[i] = v;
+                }
+                ++s;
+                if (!changed) break;
+            }
+            if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
+        }
+        if (Upre_log)
+            for (i = 0; i <= N; ++i) Upre_log[k * (N + 1) + i] = Unew[i];
+        for (i = 0; i <= N; ++i) W[i] = wk[i];
+        /* causal sweep, both directions, until nothing changes */
+        {
+            long rounds = 0;
+            int changed;
+            do {
+                changed = 0;
+                ++rounds;
+                for (i = 1; i <= N; ++i)
+                    if (W[i] == 1 && Unew[i] < Unew[i - 1] && Unew[i - 1] < INF) {
+                        Unew[i] = Unew[i - 1];
+                        changed = 1;
+                    }
+                for (i = N - 1; i >= 0; --i)
+                    if (W[i] == -1 && Unew[i] < Unew[i + 1] && Unew[i + 1] < INF) {
+                        Unew[i] = Unew[i + 1];
+                        changed = 1;
+                    }
+            } while (changed);
+            if (rounds > S0.causal_rounds_max) S0.causal_rounds_max = rounds;
+        }
+        memcpy(U, Unew, sizeof(double) * (size_t)(N + 1));
+        delta = 0.0;
+        for (i = 0; i <= N; ++i)
+            if (!(U[i] == Uprev[i]) && fabs(U[i] - Uprev[i]) > delta) delta = fabs(U[i] - Uprev[i]);
+    }
+    S0.last_delta = (S0.iters >= 1) ? delta : INF;
+    /* patched fine solution: coarse nodes take u^k, the rest their subinterval */
+    for (j = 0; j < nf; ++j) {
+        if (j % M == 0)
+            u_out[j] = uk[j / M];
+        else
+            u_out[j] = tu[j / M][j % M];
+    }
+    if (st) *st = S0;
+    for (sub = 0; sub < N; ++sub) {
+        free(tu[sub]);
+        free(tw[sub]);
+        free(te[sub]);
+    }
+    free(tu);
+    free(tw);
+    free(te);
+    free(U);
+    free(Uprev);
+    free(Unew);
+    free(uk);
+    free(Cold);
+    free(W);
+    free(wk);
+    free(cfix);
     return 0;
 }
 

@@ -92,6 +92,61 @@ double orc_theta_estimate(const orc_dd_params *p, double du, const double *dC, i
 int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
            double *u_out, double *U_out, double *delta_log, orc_dd_stats *st);
 
+/* Alg. 5 on one dense box (Step 4 of Sec. 3.2): C_H(nbrs U^k) from Uk into
+ * Cold (nullable), then the weighted sweeps into U.  Per node: fixed (Gamma,
+ * U = g), uk / wk (Alg. 4 output), Wk (W^k), axes (bit k: the node lies on a
+ * coarse line of axis k; the agreement test runs on those axes), theta.
+ * Winds are 3 bytes per node.  Returns sweeps; *capped = 1 if max_sweeps ran
+ * without a sweep that changed nothing. */
+long orc_step4_box(int d, const long *n, double H, const double *r, const unsigned char *fixed, const double *g,
+                   const double *Uk, const double *uk, const signed char *wk, const signed char *Wk,
+                   const int *axes, const double *theta, long max_sweeps, double *U, double *Cold, int *capped);
+
+/* Alg. 4's choice among the ncopies subdomain copies of one coarse-set node
+ * (enumerated axis 0 fastest, minus side first on each interface axis of B;
+ * nc[k] copies along axis k).  Returns the index of the chosen copy. */
+int orc_alg4_select(int d, int B, const int *nc, int ncopies, const double *u, const signed char *w,
+                    const unsigned char *echo, const signed char *W);
+
+/* Per-node weight of Sec. 4.2 from the history of one node: Ck = C^k,
+ * C1..C3 = C^{k-1..k-3} (C^m = C_H(nbrs U^m); the first nhist are used),
+ * uk = u^k, uprev = u^{k-1}; the constant p->theta when not adaptive or
+ * nhist < 1. */
+double orc_theta_node(const orc_dd_params *p, int nhist, double Ck, double C1, double C2, double C3, double uk,
+                      double uprev);
+
+/* orc_dd with a record of one node (fine index probe_node): probe_log[4k..4k+3]
+ * = u^k, C^k = C_H(nbrs U^k) (from Step 4 of iteration k), the weight used
+ * for U^{k+1}, and U^k; NaN where an iteration did not compute it. */
+int orc_dd_probe(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
+                 double *u_out, double *U_out, double *delta_log, orc_dd_stats *st, long probe_node,
+                 double *probe_log);
+
+/* The one-dimensional method of Sec. 3.1.  Fine grid of N*M+1 nodes, spacing
+ * h; coarse nodes every M fine nodes (H = M h). */
+typedef struct {
+    long N, M;
+    double h;
+    double theta;
+    int max_iter;
+    double tol;
+    long max_fsm_sweeps, max_coarse_sweeps;
+} orc_dd1_params;
+
+typedef struct {
+    int iters, converged;
+    double last_delta;
+    long fsm_sweeps_max, coarse_sweeps_max, fsm_cap_hits, coarse_cap_hits, causal_rounds_max;
+    long long fine_updates;
+} orc_dd1_stats;
+
+/* Steps 1-4 of Sec. 3.1 on r, gamma, g (fine grid).  u_out: patched fine
+ * solution of the last iterate.  Logs (nullable, (max_iter+1) x (N+1) each):
+ * U_log[k] = U^k, u_log[k] = u^k (Step 3's choice), W_log[k] = W^k,
+ * Upre_log[k] = the Step 4 result of iteration k before the causal sweep. */
+int orc_dd1(const orc_dd1_params *p, const double *r, const unsigned char *gamma, const double *g, double *u_out,
+            double *U_log, double *u_log, double *Upre_log, signed char *W_log, orc_dd1_stats *st);
+
 /* Discrete adjoint of the converged Godunov system at u (see oracle source):
  * given dJ/du at every node, returns dJ/dr at every node (0 on Gamma and on
  * unreached nodes). */
