@@ -35,18 +35,27 @@ _SRC = os.path.join(_HERE, "eik_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
+
+
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def _compile(out, extra):
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"] + extra + \
+        ["-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so next to its source (serial FP64, no FMA contraction)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    """Compile liboracle.so next to its source (serial FP64, no FMA contraction)
+    and liboracle_omp.so, the same source with OpenMP over the independent
+    subdomain and shifted-grid solves (the all-cores CPU baseline)."""
+    for out, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+            _compile(out, extra)
     return _LIB
 
 
@@ -87,46 +96,55 @@ class DDStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-def _load():
-    global _lib
+def _load(omp=False):
+    global _lib, _lib_omp
     with _lock:
+        if omp:
+            if _lib_omp is None:
+                build()
+                _lib_omp = _bind(ctypes.CDLL(_LIB_OMP))
+            return _lib_omp
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB)
-            dp = ctypes.POINTER(ctypes.c_double)
-            bp = ctypes.POINTER(ctypes.c_ubyte)
-            sp = ctypes.POINTER(ctypes.c_byte)
-            lp = ctypes.POINTER(ctypes.c_long)
-            lib.orc_local_solve.restype = ctypes.c_double
-            lib.orc_local_solve.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, sp]
-            lib.orc_fsm.restype = ctypes.c_long
-            lib.orc_fsm.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, sp, ctypes.c_long,
-                                    ctypes.POINTER(ctypes.c_int)]
-            lib.orc_fmm.restype = None
-            lib.orc_fmm.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp]
-            lib.orc_dd.restype = ctypes.c_int
-            lib.orc_dd.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, dp, dp, ctypes.POINTER(DDStats)]
-            lib.orc_theta_estimate.restype = ctypes.c_double
-            lib.orc_theta_estimate.argtypes = [ctypes.POINTER(DDParams), ctypes.c_double, dp, ctypes.c_int,
-                                               ctypes.c_double]
-            ip = ctypes.POINTER(ctypes.c_int)
-            lib.orc_step4_box.restype = ctypes.c_long
-            lib.orc_step4_box.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, dp, sp, sp, ip, dp,
-                                          ctypes.c_long, dp, dp, ip]
-            lib.orc_alg4_select.restype = ctypes.c_int
-            lib.orc_alg4_select.argtypes = [ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp, sp, bp, sp]
-            lib.orc_theta_node.restype = ctypes.c_double
-            lib.orc_theta_node.argtypes = [ctypes.POINTER(DDParams), ctypes.c_int] + [ctypes.c_double] * 6
-            lib.orc_dd_probe.restype = ctypes.c_int
-            lib.orc_dd_probe.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, dp, dp, ctypes.POINTER(DDStats),
-                                         ctypes.c_long, dp]
-            lib.orc_dd1.restype = ctypes.c_int
-            lib.orc_dd1.argtypes = [ctypes.POINTER(DD1Params), dp, bp, dp, dp, dp, dp, dp, sp,
-                                    ctypes.POINTER(DD1Stats)]
-            lib.orc_adjoint.restype = None
-            lib.orc_adjoint.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, dp]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+def _bind(lib):
+    """Declare the argument and result types of the oracle's C functions."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    bp = ctypes.POINTER(ctypes.c_ubyte)
+    sp = ctypes.POINTER(ctypes.c_byte)
+    lp = ctypes.POINTER(ctypes.c_long)
+    lib.orc_local_solve.restype = ctypes.c_double
+    lib.orc_local_solve.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, sp]
+    lib.orc_fsm.restype = ctypes.c_long
+    lib.orc_fsm.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, sp, ctypes.c_long,
+                            ctypes.POINTER(ctypes.c_int)]
+    lib.orc_fmm.restype = None
+    lib.orc_fmm.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp]
+    lib.orc_dd.restype = ctypes.c_int
+    lib.orc_dd.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, dp, dp, ctypes.POINTER(DDStats)]
+    lib.orc_theta_estimate.restype = ctypes.c_double
+    lib.orc_theta_estimate.argtypes = [ctypes.POINTER(DDParams), ctypes.c_double, dp, ctypes.c_int,
+                                       ctypes.c_double]
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.orc_step4_box.restype = ctypes.c_long
+    lib.orc_step4_box.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, dp, sp, sp, ip, dp,
+                                  ctypes.c_long, dp, dp, ip]
+    lib.orc_alg4_select.restype = ctypes.c_int
+    lib.orc_alg4_select.argtypes = [ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp, sp, bp, sp]
+    lib.orc_theta_node.restype = ctypes.c_double
+    lib.orc_theta_node.argtypes = [ctypes.POINTER(DDParams), ctypes.c_int] + [ctypes.c_double] * 6
+    lib.orc_dd_probe.restype = ctypes.c_int
+    lib.orc_dd_probe.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, dp, dp, ctypes.POINTER(DDStats),
+                                 ctypes.c_long, dp]
+    lib.orc_dd1.restype = ctypes.c_int
+    lib.orc_dd1.argtypes = [ctypes.POINTER(DD1Params), dp, bp, dp, dp, dp, dp, dp, sp,
+                            ctypes.POINTER(DD1Stats)]
+    lib.orc_adjoint.restype = None
+    lib.orc_adjoint.argtypes = [ctypes.c_int, lp, ctypes.c_double, dp, bp, dp, dp, dp]
+    return lib
 
 
 def _dp(a):
@@ -195,16 +213,18 @@ def fmm(r, gamma, g, h):
 
 def dd(r, gamma, g, h, tiles, c, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
        max_coarse_sweeps=80, return_coarse=False, theta_adaptive=False, omega=(1.0, 1.0, 1.0),
-       sig_gamma=0.75, sig_delta=0.01, sig_x0=0.9, theta_cap=0.0):
+       sig_gamma=0.75, sig_delta=0.01, sig_x0=0.9, theta_cap=0.0, parallel=False):
     """Two-scale DD iteration (Sec. 3.2, Steps 1-4).
 
     tiles: subdomains per axis in (x, y[, z]) order.  Returns (u, stats dict,
     delta_log[, U]) where delta_log[k] = max |U^k - U^{k-1}|.  With
     theta_adaptive the weight of Alg. 5 is estimated per node (Sec. 4.2, eq.
     secthetaest damped by eq. thetaest; omega, sig_* its parameters) and
-    `theta` is used where the estimate is undefined.
+    `theta` is used where the estimate is undefined.  parallel=True runs the
+    OpenMP build (same results; the subdomain and shifted-grid solves of a
+    step on all host cores, or OMP_NUM_THREADS).
     """
-    lib = _load()
+    lib = _load(omp=parallel)
     r, gamma, g = _prep(r, gamma, g)
     d, n = _shape_n(r.shape)
     t = list(tiles) + [1] * (3 - len(tiles))

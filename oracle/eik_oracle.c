@@ -938,6 +938,7 @@ static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned ch
     orc_dd_stats S0;
     theta_ctx tctx;
     double *thfull = NULL;
+    long *offs, *gsweeps, *gcaps, *tsweeps, *tcaps, ngrid = 0;
     memset(&S0, 0, sizeof(S0));
     if (p->d < 2 || p->d > 3 || p->c < 1) return -1;
     memset(&G, 0, sizeof(G));
@@ -979,26 +980,53 @@ static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned ch
         te[i] = malloc((size_t)tilenodes);
     }
     for (i = 0; i < G.N; ++i) U[i] = uk[i] = NAN;
+    /* the shifted coarse grids, in enumeration order */
+    {
+        long o[3];
+        int first = 1;
+        while (next_offset(&G, o, first)) {
+            first = 0;
+            ++ngrid;
+        }
+        offs = malloc(sizeof(long) * (size_t)(3 * ngrid));
+        first = 1;
+        ngrid = 0;
+        while (next_offset(&G, o, first)) {
+            first = 0;
+            offs[3 * ngrid] = o[0];
+            offs[3 * ngrid + 1] = o[1];
+            offs[3 * ngrid + 2] = o[2];
+            ++ngrid;
+        }
+    }
+    gsweeps = malloc(sizeof(long) * (size_t)ngrid);
+    gcaps = malloc(sizeof(long) * (size_t)ngrid);
+    tsweeps = malloc(sizeof(long) * (size_t)ntiles);
+    tcaps = malloc(sizeof(long) * (size_t)ntiles);
     if (probe_log) {
         for (k = 0; k < 4 * (p->max_iter + 1); ++k) probe_log[k] = NAN;
         thfull = malloc(sizeof(double) * (size_t)G.N);
         for (i = 0; i < G.N; ++i) thfull[i] = NAN;
     }
 
-    /* Step 1: every shifted coarse grid, independently; then the causal sweep. */
+    /* Step 1: every shifted coarse grid, independently; then the causal sweep.
+     * (Built with OpenMP, the grids run in parallel: each writes only its own
+     * nodes, and the counters are combined after the loop.) */
     {
-        long o[3];
-        int first = 1;
-        while (next_offset(&G, o, first)) {
-            long s;
-            first = 0;
-            s = step1_grid(&G, o, H, r, gamma, g, U, W, p->max_coarse_sweeps, &S0.coarse_cap_hits);
-            if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
-            {
-                long m[3];
-                grid_box(&G, o, m);
-                S0.coarse_updates += (long long)s * m[0] * m[1] * m[2];
-            }
+        long q;
+        for (q = 0; q < ngrid; ++q) {
+            gsweeps[q] = 0;
+            gcaps[q] = 0;
+        }
+#pragma omp parallel for schedule(dynamic, 1)
+        for (q = 0; q < ngrid; ++q)
+            gsweeps[q] = step1_grid(&G, offs + 3 * q, H, r, gamma, g, U, W, p->max_coarse_sweeps, &gcaps[q]);
+        for (q = 0; q < ngrid; ++q) {
+            long m[3];
+            if (gsweeps[q] > S0.coarse_sweeps_max) S0.coarse_sweeps_max = gsweeps[q];
+            S0.coarse_cap_hits += gcaps[q];
+            grid_box(&G, offs + 3 * q, m);
+            S0.coarse_updates += (long long)gsweeps[q] * m[0] * m[1] * m[2];
         }
     }
     {
@@ -1010,18 +1038,24 @@ static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned ch
     if (delta_log) delta_log[0] = INF;
 
     for (it = 0;; ++it) {
-        /* Steps 2 + 3: every subdomain independently. */
-        int t[3];
-        long ti = 0;
-        for (t[2] = 0; t[2] < G.T[2]; ++t[2])
-            for (t[1] = 0; t[1] < G.T[1]; ++t[1])
-                for (t[0] = 0; t[0] < G.T[0]; ++t[0]) {
-                    long s = step23_tile(&G, t, p->h, r, gamma, g, U, W, tu[ti], tw[ti], te[ti], p->max_fsm_sweeps,
-                                         &S0.fsm_cap_hits);
-                    if (s > S0.fsm_sweeps_max) S0.fsm_sweeps_max = s;
-                    S0.fine_updates += (long long)s * tilenodes;
-                    ++ti;
-                }
+        /* Steps 2 + 3: every subdomain independently (in parallel when built
+         * with OpenMP; tile ti has coordinates t, axis 0 fastest). */
+        long ti;
+        for (ti = 0; ti < ntiles; ++ti) tcaps[ti] = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (ti = 0; ti < ntiles; ++ti) {
+            int t[3];
+            t[0] = (int)(ti % G.T[0]);
+            t[1] = (int)((ti / G.T[0]) % G.T[1]);
+            t[2] = (int)(ti / ((long)G.T[0] * G.T[1]));
+            tsweeps[ti] = step23_tile(&G, t, p->h, r, gamma, g, U, W, tu[ti], tw[ti], te[ti], p->max_fsm_sweeps,
+                                      &tcaps[ti]);
+        }
+        for (ti = 0; ti < ntiles; ++ti) {
+            if (tsweeps[ti] > S0.fsm_sweeps_max) S0.fsm_sweeps_max = tsweeps[ti];
+            S0.fsm_cap_hits += tcaps[ti];
+            S0.fine_updates += (long long)tsweeps[ti] * tilenodes;
+        }
         /* Alg. 4 */
         alg4(&G, tu, tw, te, W, uk, wk);
         if (thfull) {
@@ -1043,21 +1077,20 @@ static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned ch
         tctx.C3 = it >= 3 ? Chist[(it + 1) % 4] : NULL;
         tctx.uprev = uprev;
         {
-            long o[3];
-            int first = 1;
+            long q;
             double *Unew = malloc(sizeof(double) * (size_t)G.N);
             memcpy(Unew, U, sizeof(double) * (size_t)G.N);
-            while (next_offset(&G, o, first)) {
-                long s;
-                first = 0;
-                s = step4_grid(&G, o, H, p->theta, r, gamma, g, Uprev, uk, wk, W, Unew, p->max_coarse_sweeps,
-                               &S0.coarse_cap_hits, &tctx, Chist[it % 4], thfull);
-                if (s > S0.coarse_sweeps_max) S0.coarse_sweeps_max = s;
-                {
-                    long m[3];
-                    grid_box(&G, o, m);
-                    S0.coarse_updates += (long long)s * m[0] * m[1] * m[2];
-                }
+            for (q = 0; q < ngrid; ++q) gcaps[q] = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+            for (q = 0; q < ngrid; ++q)
+                gsweeps[q] = step4_grid(&G, offs + 3 * q, H, p->theta, r, gamma, g, Uprev, uk, wk, W, Unew,
+                                        p->max_coarse_sweeps, &gcaps[q], &tctx, Chist[it % 4], thfull);
+            for (q = 0; q < ngrid; ++q) {
+                long m[3];
+                if (gsweeps[q] > S0.coarse_sweeps_max) S0.coarse_sweeps_max = gsweeps[q];
+                S0.coarse_cap_hits += gcaps[q];
+                grid_box(&G, offs + 3 * q, m);
+                S0.coarse_updates += (long long)gsweeps[q] * m[0] * m[1] * m[2];
             }
             memcpy(U, Unew, sizeof(double) * (size_t)G.N);
             free(Unew);
@@ -1122,6 +1155,11 @@ static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned ch
     free(W);
     free(wk);
     free(thfull);
+    free(offs);
+    free(gsweeps);
+    free(gcaps);
+    free(tsweeps);
+    free(tcaps);
     return 0;
 }
 

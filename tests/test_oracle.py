@@ -424,3 +424,17 @@ def test_dd_reaches_fine_solution_on_obstacles(name, kw):
     uf, _, _ = O.fsm(w["r"], w["gamma"], w["g"], w["h"])
     u, st, _ = O.dd(w["r"], w["gamma"], w["g"], w["h"], w["tiles"], w["c"], theta=0.2, max_iter=30, tol=0.0)
     assert np.abs(u - uf).max() / np.abs(uf).max() < 1e-9
+
+
+def test_parallel_oracle_build_equals_serial():
+    """The OpenMP build of the oracle (the all-cores CPU baseline) runs the
+    independent subdomain and shifted-grid solves in parallel and returns the
+    serial build's results bitwise, statistics included."""
+    n = 129
+    h = 1.0 / (n - 1)
+    r = I.sin_product((n, n), h, 0.5, 1.0 / 8)
+    gamma, g = I.point_source((n, n), (40, 90))
+    kw = dict(theta=0.3, max_iter=5, tol=0.0, max_coarse_sweeps=8)
+    u0, s0, l0 = O.dd(r, gamma, g, h, (4, 4), 8, **kw)
+    u1, s1, l1 = O.dd(r, gamma, g, h, (4, 4), 8, parallel=True, **kw)
+    assert np.array_equal(u0, u1) and s0 == s1 and np.array_equal(l0, l1, equal_nan=True)
