@@ -324,6 +324,22 @@ int eik_profile_enable(int on);
  * least one timed launch (may exceed max_entries), or EIK_ECUDA. */
 int eik_profile_collect(eik_kernel_time *out, int max_entries);
 
+/*
+ * eik_set_wait_limit: sets, on the current device, how many times a
+ * device-side wait may poll before it gives up.  The waits are the hand-offs
+ * between the warps and CTAs of a sweep and the grid barriers of the
+ * cooperative kernels; an expired wait records EIK_EDEVICE_TIMEOUT in the
+ * call's device statistics (eik_dd_stats.error, eik_fsm_stats.error, ...),
+ * makes the rest of that call return early, and never traps, so the context
+ * stays usable.  Each poll sleeps 32 ns to 1 us.  0 restores the default of
+ * 2^22 polls (seconds).  A small limit makes ordinary waits expire: it exists
+ * to test the timeout path.  It applies to work enqueued after it returns
+ * (it is a cudaMemcpyToSymbol, ordered against the legacy default stream);
+ * do not change it while a call is running.  No counterpart in the paper.
+ * Returns EIK_OK, EIK_EINVAL (negative value) or EIK_ECUDA.
+ */
+int eik_set_wait_limit(int64_t iterations);
+
 /* Thread-local description of the last non-OK status returned on this thread. */
 const char *eik_last_error(void);
 

@@ -141,14 +141,25 @@ __device__ __forceinline__ T local_solve3(const T *vm, const T *vp, T rh, uint8_
 constexpr int DEV_OK = 0;
 constexpr int DEV_TIMEOUT = -4;
 
-// Bounded spin limit for every device-side wait (iterations of at most ~1 us
-// sleep each, so an expired wait reports within seconds).
-constexpr long long SPIN_LIMIT = 1ll << 22;
+// Default iteration limit of every bounded device-side wait (iterations of at
+// most ~1 us sleep each, so an expired wait reports within seconds).
+constexpr long long SPIN_LIMIT_DEFAULT = 1ll << 22;
+
+// The limit in force.  Each translation unit that waits has its own copy per
+// device; eik_set_wait_limit writes every copy through the setter that the
+// unit defines with EIK_SPIN_LIMIT_SETTER.  A kernel that waits reads it once
+// when it starts (a global load on the path of a wait would delay the wait
+// itself).
+static __device__ long long g_spin_limit = SPIN_LIMIT_DEFAULT;
+__device__ __forceinline__ long long spin_limit() { return *(volatile const long long *)&g_spin_limit; }
+#define EIK_SPIN_LIMIT_SETTER(fname) \
+    int fname(long long v) { return (int)cudaMemcpyToSymbol(g_spin_limit, &v, sizeof(v)); }
 
 // Grid-wide barrier for cooperative launches (all CTAs co-resident).  bar[0]
-// counts arrivals, bar[1] is the generation.  The wait is bounded: on timeout
-// the error word is set and false is returned (the caller then returns).
-__device__ inline bool grid_barrier(unsigned *bar, int *err) {
+// counts arrivals, bar[1] is the generation.  The wait is bounded by `lim`
+// polls (the kernel reads spin_limit() once when it starts): on timeout the
+// error word is set and false is returned (the caller then returns).
+__device__ inline bool grid_barrier(unsigned *bar, int *err, long long lim) {
     __syncthreads();
     bool ok = true;
     if (threadIdx.x == 0) {
@@ -163,7 +174,7 @@ __device__ inline bool grid_barrier(unsigned *bar, int *err) {
         } else {
             long long it = 0;
             while (*vgen == gen) {
-                if (++it > SPIN_LIMIT) {
+                if (++it > lim) {
                     atomicExch(err, DEV_TIMEOUT);
                     ok = false;
                     break;

@@ -48,6 +48,9 @@ struct DDArgs {
     unsigned *bar;   // [2] grid barrier count / generation
     DevStats *st;
     T theta, tol;
+    // constant weight 0: every branch of Alg. 5 yields u^k exactly (u^k + 0 (U~ -
+    // C_H) = u^k), so Alg. 4 writes U^{k+1} = u^k itself and Step 4 has no sweeps
+    int step4_identity;
     int max_iter;
     long long max_fsm, max_coarse;
     // per-node weight of Sec. 4.2 (adaptive theta)
@@ -217,7 +220,7 @@ __device__ __forceinline__ void k_step1_body(const DDArgs<T> &A, char *smem, int
 // Step 4: Alg. 5 on every shifted grid.
 template <class T, bool ADAPT>
 __device__ __forceinline__ void k_step4_gen(const DDArgs<T> &A, char *smem, int gidx) {
-    if (*A.done) return;
+    if (*A.done || A.step4_identity) return;  // weight 0: Alg. 4 already wrote U^{k+1} = u^k
     const DDGeom &G = A.G;
     const GridDesc d = grid_desc(G, gidx);
     const T Hs = T(G.H);
@@ -443,6 +446,7 @@ __device__ bool causal_line_smem(const DDArgs<T> &A, bool horizontal, int line, 
 // and written in place, 32 nodes at a time.
 template <class T>
 __global__ void k_causal(DDArgs<T> A, int only_if_not_done, int lw) {
+    const long long wlim = spin_limit();  // limit of the grid-barrier waits
     if (only_if_not_done && *A.done) return;
     const DDGeom &G = A.G;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
@@ -453,7 +457,7 @@ __global__ void k_causal(DDArgs<T> A, int only_if_not_done, int lw) {
     uint8_t *sw = reinterpret_cast<uint8_t *>(su) + causal_align16((size_t)lw * sizeof(T));
     __shared__ int blk_changed;
     if (blockIdx.x == 0 && threadIdx.x < 3) A.chg[threadIdx.x] = 0;
-    if (!grid_barrier(A.bar, &A.st->err)) return;
+    if (!grid_barrier(A.bar, &A.st->err, wlim)) return;
     int rounds = 0;
     for (;;) {
         if (threadIdx.x == 0) blk_changed = 0;
@@ -467,7 +471,7 @@ __global__ void k_causal(DDArgs<T> A, int only_if_not_done, int lw) {
                 ch |= causal_line(A, true, l, 1);
             }
         }
-        if (!grid_barrier(A.bar, &A.st->err)) return;
+        if (!grid_barrier(A.bar, &A.st->err, wlim)) return;
         for (int l = gw; l <= G.ncx; l += warps_total) {
             if (lw > 0) {
                 ch |= causal_line_smem(A, false, l, su, sw);
@@ -480,7 +484,7 @@ __global__ void k_causal(DDArgs<T> A, int only_if_not_done, int lw) {
         __syncthreads();
         if (threadIdx.x == 0 && blk_changed) atomicOr(&A.chg[rounds % 3], 1);
         ++rounds;
-        if (!grid_barrier(A.bar, &A.st->err)) return;
+        if (!grid_barrier(A.bar, &A.st->err, wlim)) return;
         const int any = *(volatile int *)&A.chg[(rounds - 1) % 3];
         if (blockIdx.x == 0 && threadIdx.x == 0) A.chg[(rounds + 1) % 3] = 0;
         if (!any || rounds > 10000) break;
@@ -652,6 +656,14 @@ __device__ void alg4_body(const DDArgs<T> &A, int k, size_t bid, size_t nbid) {
         A.uk[a] = ukv;
         A.wk[a] = wkv;
         A.u_out[(size_t)Y * A.sy + X] = ukv;
+        if (A.step4_identity) {
+            // Step 4 with weight 0: U^{k+1} = u^k before the causal sweep, W = w^k
+            // (no thread reads a neighbour's U here, so the update is in place)
+            A.Uprev[a] = A.U[a];
+            A.U[a] = ukv;
+            A.W[a] = wkv;
+            continue;
+        }
         // Alg. 5 agreement bits from w^k and W^k on the axes of the node's
         // coarse lines (A = axes with index = 0 mod c)
         uint8_t m = A.gamma[(size_t)Y * A.sy + X] ? 1 : 0;
@@ -709,8 +721,9 @@ template <class T>
 __device__ void check_body(const DDArgs<T> &A, int k) {
     if (*A.done) return;
     const double delta = A.deltas[k];
-    const bool conv = k >= 1 && delta < (double)A.tol;
-    if (k == A.max_iter || conv) {
+    const bool failed = A.st->err != DEV_OK;  // an expired wait: later stages would only repeat it
+    const bool conv = k >= 1 && delta < (double)A.tol && !failed;
+    if (k == A.max_iter || conv || failed) {
         *A.done = 1;
         A.st->iters = k;
         A.st->converged = conv ? 1 : 0;

@@ -26,6 +26,8 @@
 
 namespace eik {
 
+EIK_SPIN_LIMIT_SETTER(set_spin_limit_adj)
+
 struct AdjDev {
     unsigned long long sweeps;
     int converged;

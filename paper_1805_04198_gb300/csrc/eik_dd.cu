@@ -30,6 +30,8 @@
 
 namespace eik {
 
+EIK_SPIN_LIMIT_SETTER(set_spin_limit_dd)
+
 // Kernel entry points.  Register caps keep two 9-warp subdomain CTAs per SM in
 // FP32 and let a 9-warp coarse-grid CTA fit the register file in FP64.
 #define EIK_KERNEL_PAIR(name, RF, RD)                                                  \
@@ -149,6 +151,7 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     A.sy = grid->stride[1];
     dd_layout<T>(P, &A, ws, p->max_iter);
     A.theta = (T)p->theta;
+    A.step4_identity = (!P.adaptive && p->theta == 0.0) ? 1 : 0;
     A.tol = (T)p->tol;
     A.max_iter = p->max_iter;
     A.max_fsm = p->max_fsm_sweeps;
@@ -169,12 +172,15 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     if ((rc = cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr"))) return rc;
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((int)P.fine_smem > smem_optin || (int)P.step1_smem > smem_optin || (int)P.step4_smem > smem_optin) {
-        set_error("shared memory need (%zu, %zu, %zu) exceeds the device limit %d", P.fine_smem, P.step1_smem,
+    auto finek = DDKernels<T>::fine;
+    const int fine_threads = 32 * G.tnb;
+    const size_t fine_smem = P.fine_smem;
+    if ((int)fine_smem > smem_optin || (int)P.step1_smem > smem_optin || (int)P.step4_smem > smem_optin) {
+        set_error("shared memory need (%zu, %zu, %zu) exceeds the device limit %d", fine_smem, P.step1_smem,
                   P.step4_smem, smem_optin);
         return EIK_EUNSUPPORTED;
     }
-    if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::fine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.fine_smem),
+    if ((rc = cuda_check(cudaFuncSetAttribute(finek, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fine_smem),
                          "smem attr fine")))
         return rc;
     if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.step1_smem),
@@ -211,11 +217,14 @@ static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, con
     };
     if ((rc = launch_causal(0))) return rc;
     for (int k = 0; k <= p->max_iter; ++k) {
-        EIK_LAUNCH("dd_fine_subdomains", s, DDKernels<T>::fine<<<ntiles, 32 * G.tnb, P.fine_smem, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd_fine_subdomains", s, finek<<<ntiles, fine_threads, fine_smem, s>>>(A)); ++nl;
         EIK_LAUNCH("dd_alg4_restrict", s, k_alg4<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
         EIK_LAUNCH("dd_check", s, k_check<T><<<1, 1, 0, s>>>(A, k)); ++nl;
         if (k == p->max_iter) break;
-        EIK_LAUNCH("dd_step4_weighted", s, step4k<<<G.ngrids, P.grid_threads, P.step4_smem, s>>>(A)); ++nl;
+        if (!A.step4_identity) {
+            EIK_LAUNCH("dd_step4_weighted", s, step4k<<<G.ngrids, P.grid_threads, P.step4_smem, s>>>(A));
+            ++nl;
+        }
         if ((rc = launch_causal(1))) return rc;
         EIK_LAUNCH("dd_delta", s, k_delta<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
     }

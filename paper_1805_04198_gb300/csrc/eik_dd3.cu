@@ -23,6 +23,8 @@
 
 namespace eik {
 
+EIK_SPIN_LIMIT_SETTER(set_spin_limit_dd3)
+
 struct Grid3 {
     int ox, oy, oz, mx, my, mz;
     long long off;  // element offset in the coarse arrays ([z][y][x] box)
@@ -59,6 +61,9 @@ struct DD3Args {
     unsigned *bar;
     DevStats3 *st;
     T theta, tol;
+    // constant weight 0: Alg. 5 yields u^k at every node, Alg. 4 writes
+    // U^{k+1} = u^k itself and Step 4 is not launched
+    int step4_identity;
     int max_iter;
     long long max_fsm, max_coarse;
     // per-node weight of Sec. 4.2 (adaptive = 1): weights, damping, cap, the
@@ -592,6 +597,13 @@ __global__ void k3_alg4(DD3Args<T> A) {
         A.wk[a] = wkv;
         const size_t f = fidx(A, Xg[0], Xg[1], Xg[2]);
         A.u_out[f] = ukv;
+        if (A.step4_identity) {
+            // Step 4 with weight 0: U^{k+1} = u^k before the causal sweep, W = w^k
+            A.Uprev[a] = A.U[a];
+            A.U[a] = ukv;
+            A.W[a] = wkv;
+            continue;
+        }
         uint8_t m = A.gamma[f] ? 1 : 0;
         for (int ax = 0; ax < 3; ++ax) {
             const bool on = Xg[ax] % G.c == 0;
@@ -607,8 +619,9 @@ template <class T>
 __global__ void k3_check(DD3Args<T> A, int k) {
     if (*A.done) return;
     const double delta = A.deltas[k];
-    const bool conv = k >= 1 && delta < (double)A.tol;
-    if (k == A.max_iter || conv) {
+    const bool failed = A.st->err != DEV_OK;  // an expired wait: later stages would only repeat it
+    const bool conv = k >= 1 && delta < (double)A.tol && !failed;
+    if (k == A.max_iter || conv || failed) {
         *A.done = 1;
         A.st->iters = k;
         A.st->converged = conv ? 1 : 0;
@@ -687,6 +700,7 @@ __device__ bool causal3_line(const DD3Args<T> &A, int e, int c1, int c2, int rev
 
 template <class T>
 __global__ void k3_causal(DD3Args<T> A, int only_if_not_done) {
+    const long long wlim = spin_limit();  // limit of the grid-barrier waits
     if (only_if_not_done && *A.done) return;
     const DD3Geom &G = A.G;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
@@ -694,7 +708,7 @@ __global__ void k3_causal(DD3Args<T> A, int only_if_not_done) {
     const int lane = threadIdx.x & 31;
     __shared__ int blk_changed;
     if (blockIdx.x == 0 && threadIdx.x < 3) A.chg[threadIdx.x] = 0;
-    if (!grid_barrier(A.bar, &A.st->err)) return;
+    if (!grid_barrier(A.bar, &A.st->err, wlim)) return;
     int rounds = 0;
     for (;;) {
         if (threadIdx.x == 0) blk_changed = 0;
@@ -709,13 +723,13 @@ __global__ void k3_causal(DD3Args<T> A, int only_if_not_done) {
                 ch |= causal3_line(A, e, c1, c2, 0);
                 ch |= causal3_line(A, e, c1, c2, 1);
             }
-            if (!grid_barrier(A.bar, &A.st->err)) return;
+            if (!grid_barrier(A.bar, &A.st->err, wlim)) return;
         }
         if (lane == 0 && ch) atomicOr(&blk_changed, 1);
         __syncthreads();
         if (threadIdx.x == 0 && blk_changed) atomicOr(&A.chg[rounds % 3], 1);
         ++rounds;
-        if (!grid_barrier(A.bar, &A.st->err)) return;
+        if (!grid_barrier(A.bar, &A.st->err, wlim)) return;
         const int any = *(volatile int *)&A.chg[(rounds - 1) % 3];
         if (blockIdx.x == 0 && threadIdx.x == 0) A.chg[(rounds + 1) % 3] = 0;
         if (!any || rounds > 10000) break;
@@ -906,6 +920,7 @@ static int dd3_run_t(const eik_grid *grid, const void *r, const uint8_t *gamma, 
     A.max_fsm = p->max_fsm_sweeps;
     A.max_coarse = p->max_coarse_sweeps;
     A.adaptive = P.adaptive ? 1 : 0;
+    A.step4_identity = (!P.adaptive && p->theta == 0.0) ? 1 : 0;
     for (int s2 = 0; s2 < 3; ++s2) A.om[s2] = p->omega[s2];
     A.sg = p->sig_gamma;
     A.sd = p->sig_delta;
@@ -956,7 +971,10 @@ static int dd3_run_t(const eik_grid *grid, const void *r, const uint8_t *gamma, 
         EIK_LAUNCH("dd3_alg4_restrict", s, k3_alg4<T><<<cgrid, ew, 0, s>>>(A)); ++nl;
         EIK_LAUNCH("dd3_check", s, k3_check<T><<<1, 1, 0, s>>>(A, k)); ++nl;
         if (k == p->max_iter) break;
-        EIK_LAUNCH("dd3_step4_weighted", s, k3_step4<T><<<G.ng, P.grid_threads, P.grid_smem, s>>>(A, k)); ++nl;
+        if (!A.step4_identity) {
+            EIK_LAUNCH("dd3_step4_weighted", s, k3_step4<T><<<G.ng, P.grid_threads, P.grid_smem, s>>>(A, k));
+            ++nl;
+        }
         if ((rc = launch_causal(1))) return rc;
         EIK_LAUNCH("dd3_delta", s, k3_delta<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
     }

@@ -37,6 +37,8 @@
 
 namespace eik {
 
+EIK_SPIN_LIMIT_SETTER(set_spin_limit_batch)
+
 // Flat list of items over problems: problem p owns items [pre[p], pre[p+1]).
 struct Segs {
     const int *pre;  // [n + 1]
@@ -185,6 +187,7 @@ __global__ void kb_finalize(const DDArgs<T> *__restrict__ args, BatchCtl C, eik_
 template <class T>
 __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, BatchCtl C, int only_if_not_done,
                           int lw) {
+    const long long wlim = spin_limit();  // limit of the grid-barrier waits
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -193,7 +196,7 @@ __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, 
     uint8_t *sw = reinterpret_cast<uint8_t *>(su) + causal_align16((size_t)lw * sizeof(T));
     __shared__ int blk_changed;
     if (blockIdx.x == 0 && threadIdx.x < 3) C.chg[threadIdx.x] = 0;
-    if (!grid_barrier(C.bar, C.err)) return;
+    if (!grid_barrier(C.bar, C.err, wlim)) return;
     int rounds = 0;
     for (;;) {
         if (threadIdx.x == 0) blk_changed = 0;
@@ -210,7 +213,7 @@ __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, 
                 ch |= causal_line(A, true, local, 1);
             }
         }
-        if (!grid_barrier(C.bar, C.err)) return;
+        if (!grid_barrier(C.bar, C.err, wlim)) return;
         for (int l = gw; l < vl.total; l += warps_total) {
             int local;
             const DDArgs<T> &A = args[seg_find(vl.pre, vl.n, l, local)];
@@ -226,7 +229,7 @@ __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, 
         __syncthreads();
         if (threadIdx.x == 0 && blk_changed) atomicOr(&C.chg[rounds % 3], 1);
         ++rounds;
-        if (!grid_barrier(C.bar, C.err)) return;
+        if (!grid_barrier(C.bar, C.err, wlim)) return;
         const int any = *(volatile int *)&C.chg[(rounds - 1) % 3];
         if (blockIdx.x == 0 && threadIdx.x == 0) C.chg[(rounds + 1) % 3] = 0;
         if (!any || rounds > 10000) break;
@@ -464,6 +467,7 @@ static int batch_run(int nprob, const eik_grid *grids, const void *const *r, con
         A.sy = grids[p].stride[1];
         dd_layout<T>(B.P[p], &A, base + B.region[p], params[p].max_iter);
         A.theta = (T)params[p].theta;
+        A.step4_identity = (!params[p].theta_adaptive && params[p].theta == 0.0) ? 1 : 0;
         A.tol = (T)params[p].tol;
         A.max_iter = params[p].max_iter;
         A.max_fsm = params[p].max_fsm_sweeps;

@@ -20,6 +20,8 @@
 
 namespace eik {
 
+EIK_SPIN_LIMIT_SETTER(set_spin_limit_fsm)
+
 static thread_local char g_err[512];
 
 // ---- optional per-launch event timing -------------------------------------
@@ -494,7 +496,30 @@ using namespace eik;
 
 extern "C" const char *eik_last_error(void) { return g_err; }
 
-extern "C" int eik_version(void) { return 101; }
+extern "C" int eik_version(void) { return 102; }
+
+namespace eik {
+int set_spin_limit_dd(long long);
+int set_spin_limit_batch(long long);
+int set_spin_limit_dd3(long long);
+int set_spin_limit_fsm3(long long);
+int set_spin_limit_adj(long long);
+}  // namespace eik
+
+extern "C" int eik_set_wait_limit(int64_t iterations) {
+    if (iterations < 0) {
+        set_error("eik_set_wait_limit: iterations must be >= 0 (0 restores the default)");
+        return EIK_EINVAL;
+    }
+    const long long v = iterations == 0 ? SPIN_LIMIT_DEFAULT : (long long)iterations;
+    int (*const setters[])(long long) = {set_spin_limit_fsm, set_spin_limit_dd, set_spin_limit_batch,
+                                         set_spin_limit_dd3, set_spin_limit_fsm3, set_spin_limit_adj};
+    for (auto f : setters) {
+        const int rc = cuda_check((cudaError_t)f(v), "cudaMemcpyToSymbol(wait limit)");
+        if (rc) return rc;
+    }
+    return EIK_OK;
+}
 
 extern "C" int eik_profile_enable(int on) {
     int prev = g_prof_on ? 1 : 0;

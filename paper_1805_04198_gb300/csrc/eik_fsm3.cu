@@ -18,6 +18,8 @@
 
 namespace eik {
 
+EIK_SPIN_LIMIT_SETTER(set_spin_limit_fsm3)
+
 struct Fsm3Dev {
     unsigned long long sweeps;
     int converged;
@@ -62,6 +64,7 @@ __global__ void k_fsm3_init(Fsm3Args<T> A) {
 
 template <class T>
 __global__ void k_fsm3_sweeps(Fsm3Args<T> A) {
+    const long long wlim = spin_limit();  // limit of the grid-barrier waits
     const T INF = Num<T>::inf();
     const int nx = A.nx, ny = A.ny, nz = A.nz;
     const size_t plane = (size_t)nx * ny;
@@ -102,13 +105,13 @@ __global__ void k_fsm3_sweeps(Fsm3Args<T> A) {
                     ch = true;
                 }
             }
-            if (!grid_barrier(A.dev->bar, &A.dev->err)) return;
+            if (!grid_barrier(A.dev->bar, &A.dev->err, wlim)) return;
         }
         // sweep k changed something?  slot k % 3, cleared two sweeps ahead
         if (ch) blk_ch = 1;
         __syncthreads();
         if (threadIdx.x == 0 && blk_ch) atomicOr(&A.dev->chg[k % 3], 1);
-        if (!grid_barrier(A.dev->bar, &A.dev->err)) return;
+        if (!grid_barrier(A.dev->bar, &A.dev->err, wlim)) return;
         const int any = *(volatile int *)&A.dev->chg[k % 3];
         if (blockIdx.x == 0 && threadIdx.x == 0) A.dev->chg[(k + 2) % 3] = 0;
         if (!any) {

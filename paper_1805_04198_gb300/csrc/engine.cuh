@@ -111,6 +111,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Shared control words of one engine run.
 struct EngineCtl {
+    long long lim;  // polls a wait may make (read once when the run starts)
     int *prog;      // [nb] hand-off progress: (sweep << SWEEP_SHIFT) | rows published
     int *done;      // [nb] sweeps completed by the block (all rows written back)
     int *fin;       // [8] warps that finished sweep k (slot k & 7)
@@ -137,7 +138,7 @@ __device__ __forceinline__ bool wait_ge(const int *p, int target, const EngineCt
     unsigned ns = 32;
     while (vload(p) < target) {
         if (vload(C.abort_flag) || vload(C.stop_at) < sweep) return false;
-        if (++it > SPIN_LIMIT) {
+        if (++it > C.lim) {
             vstore(C.abort_flag, 1);
             atomicExch(err, DEV_TIMEOUT);
             return false;
@@ -389,6 +390,7 @@ __device__ void engine_run(const Box<T, NST> &bx, const P &pol, long long max_sw
     uint8_t *sbring = bytes + (size_t)warp * sb_b;
     int *ints = GLOBAL ? gctl : reinterpret_cast<int *>(bytes + (size_t)nwc * sb_b);
     EngineCtl C;
+    C.lim = spin_limit();
     C.abort_flag = ints;
     C.stop_at = ints + 1;
     C.fin = ints + 8;

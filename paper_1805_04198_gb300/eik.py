@@ -8,7 +8,7 @@ Entry points mirror the C names:
     eik_fsm_workspace_size, eik_fsm, eik_dd_workspace_size, eik_dd_solve,
     eik_dd_batched_workspace_size, eik_dd_solve_batched, eik_dd_batched_autotune,
     eik_fsm_many_workspace_size, eik_fsm_many, eik_dd_adjoint_many_workspace_size,
-    eik_dd_adjoint_many, eik_last_error, eik_version
+    eik_dd_adjoint_many, eik_set_wait_limit, eik_last_error, eik_version
 plus the conveniences :func:`fsm` and :func:`dd_solve`, which allocate the
 workspace and the output with torch and return host-side statistics.
 """
@@ -130,6 +130,8 @@ def load():
         lib.eik_dd_adjoint_many.restype = ctypes.c_int
         lib.eik_dd_adjoint_many.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, vp, pp, pp, pp, pp, vp,
                                             ctypes.c_int64, vp, ctypes.c_size_t, vp, vp]
+        lib.eik_set_wait_limit.restype = ctypes.c_int
+        lib.eik_set_wait_limit.argtypes = [ctypes.c_int64]
         lib.eik_profile_enable.restype = ctypes.c_int
         lib.eik_profile_enable.argtypes = [ctypes.c_int]
         lib.eik_profile_collect.restype = ctypes.c_int
@@ -144,6 +146,12 @@ def eik_last_error() -> str:
 
 def eik_version() -> int:
     return load().eik_version()
+
+
+def eik_set_wait_limit(iterations: int) -> None:
+    """Polls a device-side wait may make before it reports EIK_EDEVICE_TIMEOUT
+    (current device; 0 restores the default)."""
+    _check(load().eik_set_wait_limit(int(iterations)))
 
 
 def _check(code):

@@ -64,3 +64,17 @@ def test_calls_reject_null_and_small_workspace(lib):
     assert rc == -2 and "workspace" in lib.eik_last_error()
     rc = so.eik_fsm(ctypes.byref(g), fake, fake, fake, fake, 0, fake, 1 << 30, null, null)
     assert rc == -1
+
+
+def test_wait_limit_rejects_negative_before_cuda_work(lib):
+    so = lib.load()
+    assert so.eik_set_wait_limit(-1) == -1
+    assert "iterations" in lib.eik_last_error()
+
+
+def test_noalloc_scratch_size_matches_header(lib):
+    """The binding's size check mirrors the header's #define."""
+    hdr = open(os.path.join(ROOT, "include", "eik.h")).read()
+    m = re.search(r"#define\s+EIK_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", hdr)
+    assert m, "EIK_NOALLOC_SCRATCH_BYTES not found in eik.h"
+    assert lib.NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))

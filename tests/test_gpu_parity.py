@@ -86,6 +86,8 @@ def _dd_case(n, tiles, c, amp=0.5, eps=0.25, src=None):
     (97, (3, 3), 16, 0.2, 5),     # 33-node subdomains: two blocks, ragged tail
     (129, (2, 2), 8, 0.3, 4),     # 65-node subdomains, c < S
     (73, (3, 3), 6, 0.2, 3),      # coarse ratio not a power of two
+    (65, (4, 4), 8, 0.0, 6),      # weight 0: Alg. 4 hands u^k to the causal sweep, no Step 4 sweeps
+    (97, (3, 3), 16, 0.0, 5),
 ])
 def test_dd_fp64_bitwise(gpu, n, tiles, c, theta, kmax):
     r, gamma, g, h = _dd_case(n, tiles, c)
@@ -397,6 +399,7 @@ def _dd3_case(n, amp=0.4, eps=0.25, src=None):
     (17, (2, 2, 2), 8, 0.2, 3),    # c equal to the subdomain width
     (25, (3, 3, 3), 4, 0.5, 3),
     (17, (1, 2, 4), 2, 1.0, 2),    # anisotropic tiling, theta = 1
+    (17, (2, 2, 2), 4, 0.0, 4),    # weight 0: Alg. 4 hands u^k to the causal sweep, no Step 4 sweeps
 ])
 def test_dd3_fp64_bitwise(gpu, n, tiles, c, theta, kmax):
     r, gamma, g, h = _dd3_case(n, src=(n // 2, n // 3, n // 2))
@@ -419,6 +422,40 @@ def test_dd3_fp32_converged_against_oracle(gpu):
                          **args)
     assert s_ref["converged"] == 1 and st["converged"] == 1
     assert _rel(u.cpu().numpy().astype(np.float64), u_ref) <= TOL32
+
+
+def test_dd3_fp32_box_shape_of_the_257_cube(gpu):
+    """65^3 in 2^3 subdomains of 33^3 nodes with coarse ratio 8: the subdomain
+    and coarse-grid box shapes of the 257^3 workload (every thread of the 3-D
+    subdomain kernel owns three columns and uses every prefetch slot).  The
+    converged FP32 solve against the oracle's FP64 full-grid solution u^f at
+    every node."""
+    n = 65
+    h = 1.0 / (n - 1)
+    r = I.sin_product((n, n, n), h, 0.4, 1.0 / 8)
+    gamma, g = I.point_source((n, n, n), (32, 32, 32))
+    r32 = r.astype(np.float32)
+    uf, _, conv = O.fsm(r32.astype(np.float64), gamma, g, h)
+    assert conv
+    u, st = gpu.dd_solve(_t(r32, torch.float32), _t(gamma, torch.uint8), _t(g, torch.float32), h, (2, 2, 2), 8,
+                         theta=0.0, max_iter=40, tol=1e-6, max_coarse_sweeps=8)
+    assert st["converged"] == 1 and st["error"] == 0
+    assert _rel(u.cpu().numpy().astype(np.float64), uf) <= TOL32
+
+
+def test_dd3_full_size_257_against_oracle_fsm(gpu):
+    """The 257^3 workload (8^3 subdomains, coarse ratio 8, FP32, weight 0,
+    stop at a coarse update below 1e-6) in the launch configuration the
+    benchmark times, run to convergence, against the oracle's FP64 full-grid
+    FSM solution at every node."""
+    w = I.workload_c2()
+    r32 = w["r"].astype(np.float32)
+    uf, _, conv = O.fsm(r32.astype(np.float64), w["gamma"], w["g"], w["h"])
+    assert conv
+    u, st = gpu.dd_solve(_t(r32, torch.float32), _t(w["gamma"], torch.uint8), _t(w["g"], torch.float32), w["h"],
+                         w["tiles"], w["c"], theta=0.0, max_iter=80, tol=1e-6, max_coarse_sweeps=8)
+    assert st["converged"] == 1 and st["error"] == 0
+    assert _rel(u.cpu().numpy().astype(np.float64), uf) <= TOL32
 
 
 # --------------------------------------------------------------------------
