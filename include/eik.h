@@ -282,8 +282,9 @@ int eik_dd_batched_autotune(int nprob, const eik_grid *grids, const void *const 
 
 /*
  * eik_dd_solve_noalloc: eik_dd_solve for callers that cannot allocate device
- * memory (for example while a CUDA graph is being captured, or when another
- * runtime owns the allocator).  It takes no workspace: the scratch is a static
+ * memory (for example a host whose device allocator belongs to another runtime
+ * that must not be bypassed, or a real-time loop that forbids allocation once
+ * it runs).  It takes no workspace: the scratch is a static
  * device array of EIK_NOALLOC_SCRATCH_BYTES inside the library, which every
  * GPU that loads the library keeps until the process exits.  This entry point
  * has no counterpart in the paper; it only changes where the scratch lives.

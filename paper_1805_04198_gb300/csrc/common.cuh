@@ -137,6 +137,13 @@ __device__ __forceinline__ T local_solve3(const T *vm, const T *vp, T rh, uint8_
     return u;
 }
 
+// Register cap of a sweep-engine kernel by element type (FP32, FP64): keeps
+// the single-CTA launch shapes (up to 32 warps) and the co-residency of the
+// cooperative multi-CTA forms.
+template <class T, int F32, int F64> struct RegCap {
+    static constexpr int v = sizeof(T) == 4 ? F32 : F64;
+};
+
 // Status codes mirrored from eik.h for device code.
 constexpr int DEV_OK = 0;
 constexpr int DEV_TIMEOUT = -4;

@@ -214,7 +214,7 @@ __device__ void adj_run_body(const AdjArgs<T> &A, char *smem) {
 }
 
 template <class T>
-__global__ void k_adj_run(AdjArgs<T> A) {
+__global__ void __maxnreg__((RegCap<T, 152, 176>::v)) k_adj_run(AdjArgs<T> A) {
     extern __shared__ __align__(16) char smem[];
     adj_run_body(A, smem);
 }
@@ -239,7 +239,7 @@ __device__ void adj_run_global_body(const AdjArgs<T> &A, char *smem, int cta) {
 }
 
 template <class T>
-__global__ void k_adj_run_global(AdjArgs<T> A) {
+__global__ void __maxnreg__((RegCap<T, 152, 176>::v)) k_adj_run_global(AdjArgs<T> A) {
     extern __shared__ __align__(16) char smem[];
     adj_run_global_body(A, smem, (int)blockIdx.x);
 }
@@ -338,7 +338,7 @@ static int adj_run(const eik_grid *grid, const AdjPlan &P, const void *r, const 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncAttributes fa;
     if ((rc = cuda_check(cudaFuncGetAttributes(&fa, k_adj_run<T>), "func attr"))) return rc;
-    const bool single = (int)P.smem <= optin && P.nb <= 32 && (long long)fa.numRegs * 32 * P.nb <= 65536;
+    const bool single = (int)P.smem <= optin && P.nb <= 32 && regs_fit(fa, P.nb);
     A.launches = single ? 5 : 6;
     const size_t total = (size_t)P.nx * P.ny;
     const int tb = (int)std::min<size_t>((total + 255) / 256, (size_t)nsm * 16);
@@ -425,7 +425,7 @@ __global__ void k_adjm_pack(AdjMany<T> M) {
     adj_pack_body(adj_prob(M, blockIdx.y), blockIdx.x, gridDim.x);
 }
 template <class T>
-__global__ void k_adjm_run(AdjMany<T> M) {
+__global__ void __maxnreg__((RegCap<T, 152, 176>::v)) k_adjm_run(AdjMany<T> M) {
     extern __shared__ __align__(16) char smem[];
     adj_run_body(adj_prob(M, blockIdx.x), smem);
 }
@@ -437,7 +437,7 @@ __global__ void k_adjm_init_global(AdjMany<T> M) {
 }
 // CTA c of the launch serves problem p0 + c / nblk as its CTA c % nblk
 template <class T>
-__global__ void k_adjm_run_global(AdjMany<T> M, int p0, int nblk) {
+__global__ void __maxnreg__((RegCap<T, 160, 160>::v)) k_adjm_run_global(AdjMany<T> M, int p0, int nblk) {
     extern __shared__ __align__(16) char smem[];
     adj_run_global_body(adj_prob(M, p0 + (int)blockIdx.x / nblk), smem, (int)blockIdx.x % nblk);
 }
@@ -522,7 +522,7 @@ static int adj_many_run(const eik_grid *grid, const AdjManyPlan &MP, int nprob, 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncAttributes fa;
     if ((rc = cuda_check(cudaFuncGetAttributes(&fa, k_adjm_run<T>), "func attr"))) return rc;
-    const bool single = (int)P.smem <= optin && P.nb <= 32 && (long long)fa.numRegs * 32 * P.nb <= 65536;
+    const bool single = (int)P.smem <= optin && P.nb <= 32 && regs_fit(fa, P.nb);
     const int nblk = (P.nb + P.wpc - 1) / P.wpc;
     int group = nprob;
     if (!single) {

@@ -33,7 +33,9 @@ namespace eik {
 EIK_SPIN_LIMIT_SETTER(set_spin_limit_dd)
 
 // Kernel entry points.  Register caps keep two 9-warp subdomain CTAs per SM in
-// FP32 and let a 9-warp coarse-grid CTA fit the register file in FP64.
+// FP32 and let a 9-warp CTA fit the register file in FP64 (it is split across
+// the SM's four schedulers, 16 K registers each, and 3 of the 9 warps share
+// one: at most 168 registers a thread).
 #define EIK_KERNEL_PAIR(name, RF, RD)                                                  \
     __global__ void __maxnreg__(RF) name##_f32(DDArgs<float> A) {                     \
         extern __shared__ __align__(16) char smem[];                                  \
@@ -43,10 +45,10 @@ EIK_SPIN_LIMIT_SETTER(set_spin_limit_dd)
         extern __shared__ __align__(16) char smem[];                                  \
         name##_body<double>(A, smem, blockIdx.x);                                     \
     }
-EIK_KERNEL_PAIR(k_step1, 96, 224)
-EIK_KERNEL_PAIR(k_step4, 160, 224)
-EIK_KERNEL_PAIR(k_step4a, 160, 224)
-EIK_KERNEL_PAIR(k_fine, 96, 224)
+EIK_KERNEL_PAIR(k_step1, 96, 168)
+EIK_KERNEL_PAIR(k_step4, 160, 168)
+EIK_KERNEL_PAIR(k_step4a, 160, 168)
+EIK_KERNEL_PAIR(k_fine, 96, 168)
 
 template <class T> struct DDKernels;
 template <> struct DDKernels<float> {
@@ -270,10 +272,9 @@ extern "C" int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *
 // Entry point that allocates nothing: the DD workspace lives in a file-scope
 // device array instead of caller memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA graph
-// that is being captured (allocation calls are not capturable), hosts whose
-// allocator is owned by another runtime that must not be bypassed, and
-// real-time loops that forbid allocation after start-up.  For them the scratch
+// Some callers cannot call cudaMalloc at all: hosts whose allocator is owned
+// by another runtime that must not be bypassed, and real-time loops that
+// forbid allocation after start-up.  For them the scratch
 // is a static __device__ array of EIK_NOALLOC_SCRATCH_BYTES (32 MiB), which
 // every GPU that loads this library keeps until the process exits.
 // --------------------------------------------------------------------------

@@ -240,7 +240,8 @@ __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, 
     }
 }
 
-// Box stages: the same register caps as the single-problem kernels.
+// Box stages: the same register caps as the single-problem kernels (FP64: a
+// 9-warp CTA, 3 warps per scheduler, at most 168 registers a thread).
 #define EIK_BATCH_PAIR(name, body, RF, RD)                                                         \
     __global__ void __maxnreg__(RF) name##_f32(const DDArgs<float> *__restrict__ args, ItemList L) { \
         extern __shared__ __align__(16) char smem[];                                               \
@@ -250,10 +251,10 @@ __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, 
         extern __shared__ __align__(16) char smem[];                                               \
         for_items(L, [&](int p, int local) { body<double>(args[p], smem, local); });               \
     }
-EIK_BATCH_PAIR(kb_step1, k_step1_body, 96, 224)
-EIK_BATCH_PAIR(kb_step4, k_step4_body, 160, 224)
-EIK_BATCH_PAIR(kb_step4a, k_step4a_body, 160, 224)
-EIK_BATCH_PAIR(kb_fine, k_fine_body, 96, 224)
+EIK_BATCH_PAIR(kb_step1, k_step1_body, 96, 168)
+EIK_BATCH_PAIR(kb_step4, k_step4_body, 160, 168)
+EIK_BATCH_PAIR(kb_step4a, k_step4a_body, 160, 168)
+EIK_BATCH_PAIR(kb_fine, k_fine_body, 96, 168)
 
 template <class T> struct BatchKernels;
 template <> struct BatchKernels<float> {

@@ -159,7 +159,7 @@ __device__ void fsm_run_body(const FsmArgs<T> &A, char *smem) {
 }
 
 template <class T>
-__global__ void k_fsm_run(FsmArgs<T> A) {
+__global__ void __maxnreg__((RegCap<T, 96, 128>::v)) k_fsm_run(FsmArgs<T> A) {
     extern __shared__ __align__(16) char smem[];
     fsm_run_body(A, smem);
 }
@@ -193,7 +193,7 @@ __device__ void fsm_run_global_body(const FsmArgs<T> &A, char *smem, int cta) {
 }
 
 template <class T>
-__global__ void k_fsm_run_global(FsmArgs<T> A) {
+__global__ void __maxnreg__((RegCap<T, 104, 160>::v)) k_fsm_run_global(FsmArgs<T> A) {
     extern __shared__ __align__(16) char smem[];
     fsm_run_global_body(A, smem, (int)blockIdx.x);
 }
@@ -284,7 +284,7 @@ static int fsm_run(const eik_grid *grid, const FsmPlan &P, const void *r, const 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncAttributes fa;
     if ((rc = cuda_check(cudaFuncGetAttributes(&fa, k_fsm_run<T>), "func attr"))) return rc;
-    const bool single = (int)P.smem <= optin && P.nb <= 32 && (long long)fa.numRegs * 32 * P.nb <= 65536;
+    const bool single = (int)P.smem <= optin && P.nb <= 32 && regs_fit(fa, P.nb);
     A.launches = single ? 3 : 4;
     const size_t total = (size_t)P.nx * P.ny;
     const int tb = (int)std::min<size_t>((total + 255) / 256, (size_t)nsm * 16);
@@ -358,7 +358,7 @@ __global__ void k_fsmm_pack(FsmMany<T> M) {
 }
 
 template <class T>
-__global__ void k_fsmm_run(FsmMany<T> M) {
+__global__ void __maxnreg__((RegCap<T, 104, 128>::v)) k_fsmm_run(FsmMany<T> M) {
     extern __shared__ __align__(16) char smem[];
     fsm_run_body(fsm_prob(M, blockIdx.x), smem);
 }
@@ -372,7 +372,7 @@ __global__ void k_fsmm_init_global(FsmMany<T> M) {
 
 // CTA c of the launch serves problem p0 + c / nblk as its CTA c % nblk
 template <class T>
-__global__ void k_fsmm_run_global(FsmMany<T> M, int p0, int nblk) {
+__global__ void __maxnreg__((RegCap<T, 96, 160>::v)) k_fsmm_run_global(FsmMany<T> M, int p0, int nblk) {
     extern __shared__ __align__(16) char smem[];
     fsm_run_global_body(fsm_prob(M, p0 + (int)blockIdx.x / nblk), smem, (int)blockIdx.x % nblk);
 }
@@ -435,7 +435,7 @@ static int fsm_many_run(const eik_grid *grid, const FsmManyPlan &MP, int nprob, 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncAttributes fa;
     if ((rc = cuda_check(cudaFuncGetAttributes(&fa, k_fsmm_run<T>), "func attr"))) return rc;
-    const bool single = (int)P.smem <= optin && P.nb <= 32 && (long long)fa.numRegs * 32 * P.nb <= 65536;
+    const bool single = (int)P.smem <= optin && P.nb <= 32 && regs_fit(fa, P.nb);
     const int nblk = (P.nb + P.wpc - 1) / P.wpc;
     int group = nprob;  // problems per cooperative launch
     if (!single) {

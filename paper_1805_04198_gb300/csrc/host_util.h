@@ -37,6 +37,16 @@ inline int cuda_check(cudaError_t e, const char *what) {
     return EIK_OK;
 }
 
+// Whether the registers of one CTA of `warps` warps of a kernel fit an SM.  The
+// register file is split evenly across the SM's four schedulers and a CTA's
+// warps are spread over them, so the busiest scheduler holds ceil(warps / 4)
+// warps; registers are allocated per thread in multiples of 8.  (A product
+// threads x registers against the whole file accepts CTAs that cannot launch.)
+inline bool regs_fit(const cudaFuncAttributes &fa, int warps, int regs_per_sm = 65536) {
+    const long long per_warp = (long long)((fa.numRegs + 7) & ~7) * 32;
+    return per_warp * ((warps + 3) / 4) <= regs_per_sm / 4;
+}
+
 inline bool valid_grid_common(const eik_grid *g, int ndim_required) {
     if (!g) {
         set_error("grid is NULL");
