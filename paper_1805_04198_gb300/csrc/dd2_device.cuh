@@ -45,6 +45,8 @@ struct DDArgs {
     int *done;
     double *deltas;  // [max_iter + 2] as doubles (max via integer atomics on bits)
     int *chg;        // [4] causal round flags + barrier
+    int *ldirty;     // [ncy+1] horizontal then [ncx+1] vertical coarse lines the causal sweep must
+                     // (re)visit; null: every line in every round
     unsigned *bar;   // [2] grid barrier count / generation
     DevStats *st;
     T theta, tol;
@@ -269,8 +271,10 @@ __device__ __forceinline__ void k_step4a_body(const DDArgs<T> &A, char *smem, in
 // One direction of one line: values v (current) with "connected to the
 // predecessor in scan order" flags; inclusive segmented max-scan per 32-node
 // chunk with a carry across chunks.
+// `cross` (nullable): flags of the crossing lines, one per coarse line of the
+// other direction; a raised intersection node marks its crossing line.
 template <class T>
-__device__ bool causal_line(const DDArgs<T> &A, bool horizontal, int line, int rev) {
+__device__ bool causal_line(const DDArgs<T> &A, bool horizontal, int line, int rev, int *cross = nullptr) {
     const DDGeom &G = A.G;
     const T INF = Num<T>::inf();
     const int lane = threadIdx.x & 31;
@@ -315,6 +319,7 @@ __device__ bool causal_line(const DDArgs<T> &A, bool horizontal, int line, int r
         if (valid && v > u) {  // values only rise; NaN never counts as a change
             A.U[a] = v;
             changed = true;
+            if (cross && p % G.c == 0) cross[p / G.c] = 1;
         }
         carry = __shfl_sync(FULL, v, 31);
         carry_orig = __shfl_sync(FULL, u, 31);
@@ -396,7 +401,8 @@ __device__ void causal_pass_smem(T *su, uint8_t *sw, int len, int rev) {
 // Both passes of Alg. 2 on one coarse line through shared memory; returns
 // whether any node was raised (warp-uniform).
 template <class T>
-__device__ bool causal_line_smem(const DDArgs<T> &A, bool horizontal, int line, T *su, uint8_t *sw) {
+__device__ bool causal_line_smem(const DDArgs<T> &A, bool horizontal, int line, T *su, uint8_t *sw,
+                                 int *cross = nullptr) {
     const DDGeom &G = A.G;
     const int lane = threadIdx.x & 31;
     const int len = horizontal ? G.nx : G.ny;
@@ -435,6 +441,7 @@ __device__ bool causal_line_smem(const DDArgs<T> &A, bool horizontal, int line, 
         if (sw[p] & 0x80) {
             A.U[coarse_addr(G, horizontal ? p : fixedc, horizontal ? fixedc : p)] = su[p];
             changed = true;
+            if (cross && p % G.c == 0) cross[p / G.c] = 1;
         }
     }
     __syncwarp();
@@ -457,6 +464,15 @@ __global__ void k_causal(DDArgs<T> A, int only_if_not_done, int lw) {
     uint8_t *sw = reinterpret_cast<uint8_t *>(su) + causal_align16((size_t)lw * sizeof(T));
     __shared__ int blk_changed;
     if (blockIdx.x == 0 && threadIdx.x < 3) A.chg[threadIdx.x] = 0;
+    // Lines share only their intersection nodes, so after the first round a
+    // line needs another pass only if a crossing line raised one of them: the
+    // flags start set, a line clears its own before its pass, and a raised
+    // intersection node sets the crossing line's.  The least fixed point is
+    // the same; lines that cannot change are skipped.
+    int *const hdirty = A.ldirty, *const vdirty = A.ldirty ? A.ldirty + G.ncy + 1 : nullptr;
+    if (A.ldirty)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.ncy + 1 + G.ncx + 1; i += gridDim.x * blockDim.x)
+            A.ldirty[i] = 1;
     if (!grid_barrier(A.bar, &A.st->err, wlim)) return;
     int rounds = 0;
     for (;;) {
@@ -464,20 +480,30 @@ __global__ void k_causal(DDArgs<T> A, int only_if_not_done, int lw) {
         __syncthreads();
         bool ch = false;
         for (int l = gw; l <= G.ncy; l += warps_total) {
+            if (hdirty) {
+                if (!vload(hdirty + l)) continue;
+                __syncwarp();
+                if (lane == 0) hdirty[l] = 0;
+            }
             if (lw > 0) {
-                ch |= causal_line_smem(A, true, l, su, sw);
+                ch |= causal_line_smem(A, true, l, su, sw, vdirty);
             } else {
-                ch |= causal_line(A, true, l, 0);
-                ch |= causal_line(A, true, l, 1);
+                ch |= causal_line(A, true, l, 0, vdirty);
+                ch |= causal_line(A, true, l, 1, vdirty);
             }
         }
         if (!grid_barrier(A.bar, &A.st->err, wlim)) return;
         for (int l = gw; l <= G.ncx; l += warps_total) {
+            if (vdirty) {
+                if (!vload(vdirty + l)) continue;
+                __syncwarp();
+                if (lane == 0) vdirty[l] = 0;
+            }
             if (lw > 0) {
-                ch |= causal_line_smem(A, false, l, su, sw);
+                ch |= causal_line_smem(A, false, l, su, sw, hdirty);
             } else {
-                ch |= causal_line(A, false, l, 0);
-                ch |= causal_line(A, false, l, 1);
+                ch |= causal_line(A, false, l, 0, hdirty);
+                ch |= causal_line(A, false, l, 1, hdirty);
             }
         }
         if (lane == 0 && ch) atomicOr(&blk_changed, 1);

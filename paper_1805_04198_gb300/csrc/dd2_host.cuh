@@ -44,6 +44,7 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
     int *done = cv.take<int>(4);
     double *deltas = cv.take<double>((size_t)max_iter + 2);
     int *chg = cv.take<int>(4);
+    int *ldirty = cv.take<int>((size_t)G.ncx + G.ncy + 2);
     unsigned *bar = cv.take<unsigned>(4);
     DevStats *st = cv.take<DevStats>(1);
     T *Ch[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -73,6 +74,7 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
         A->done = done;
         A->deltas = deltas;
         A->chg = chg;
+        A->ldirty = ldirty;
         A->bar = bar;
         A->st = st;
     }
