@@ -171,6 +171,48 @@ int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, cons
                  const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes,
                  eik_dd_stats *stats, void *stream);
 
+/*
+ * Sharded 2-D solve: the phases of eik_dd_solve for a caller that splits the
+ * subdomain solves (Steps 2-3 of Sec. 3.2, which the paper runs "in parallel"
+ * for every subdomain) over several processes, each owning a slab of
+ * subdomain rows [row0, row1) along y, while every process keeps the whole
+ * coarse state (Alg. 4, Step 4 and Alg. 2 run replicated on the same data, so
+ * the update size that stops the iteration is the same everywhere and needs no
+ * reduction).  Per iteration k = 0, 1, ...:
+ *   eik_dd_shard_fine   Steps 2-3 on the slab's subdomains; each subdomain's
+ *                       copies at its coarse-set nodes (the values Alg. 4
+ *                       chooses from) go to its record of xbuf;
+ *   the caller gathers every slab's records into its own xbuf (records of
+ *                       subdomain t at offset t * record_bytes, t = ty * tx +
+ *                       x-index, so a slab's records are one contiguous range:
+ *                       one all-gather);
+ *   eik_dd_shard_coarse the records into the copies, Alg. 4 and the stop test
+ *                       of iteration k, then (k < max_iter) Step 4, the causal
+ *                       sweep and the update size; statistics into stats
+ *                       (device) as eik_dd_solve writes them, except that
+ *                       fine_updates, fsm_sweeps_max and fsm_cap_hits count
+ *                       this process's subdomains (sum, max and sum over the
+ *                       processes give eik_dd_solve's).  The iteration stops
+ *                       after k when stats.converged, stats.error or
+ *                       k == max_iter.
+ * eik_dd_shard_start (set-up, Step 1 and its causal sweep) runs once before.
+ * Arguments are those of eik_dd_solve (workspace eik_dd_workspace_size, per
+ * process); xbuf is a device buffer of eik_dd_shard_exchange_bytes bytes,
+ * 16-byte aligned.  After the last iteration u_out holds, on every process,
+ * all coarse-set nodes and the other nodes of its own slab's subdomains.  With
+ * one slab covering every row the phases reproduce eik_dd_solve bitwise.
+ * Validation failures return EIK_EINVAL (a 3-D grid: EIK_EUNSUPPORTED).
+ */
+size_t eik_dd_shard_exchange_bytes(const eik_grid *grid, const eik_dd_params *params, size_t *record_bytes);
+int eik_dd_shard_start(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                       const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes, void *stream);
+int eik_dd_shard_fine(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                      const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes, int row0, int row1,
+                      void *xbuf, void *stream);
+int eik_dd_shard_coarse(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                        const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes, int k,
+                        const void *xbuf, eik_dd_stats *stats, void *stream);
+
 /* ------------------------------------------------------------------------- */
 /* Gradient through the converged discrete system (a project addition: the    */
 /* paper has no gradient).                                                     */

@@ -47,6 +47,7 @@ struct DDArgs {
     int *chg;        // [4] causal round flags + barrier
     int *ldirty;     // [ncy+1] horizontal then [ncx+1] vertical coarse lines the causal sweep must
                      // (re)visit; null: every line in every round
+    int tile0;       // first subdomain of a subdomain launch (a slab of a sharded solve)
     unsigned *bar;   // [2] grid barrier count / generation
     DevStats *st;
     T theta, tol;
@@ -613,6 +614,69 @@ __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int 
         if (Y % G.sy == 0 && Y > 0 && Y < G.ny - 1 && yl == 0) slot |= 2;
         A.cu[(size_t)slot * G.coarse_elems + ca] = uv;
         A.cw[(size_t)slot * G.coarse_elems + ca] = w;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Exchange records of a sharded solve: the copies (u, w) one subdomain wrote at
+// its coarse-set nodes (Step 3's output that Alg. 4 reads), in a fixed order:
+// rows yl = 0..S, in a row on a coarse line every node, in another row the
+// nodes on coarse columns.  Record = [ncs values][ncs winds], each part
+// padded to 16 bytes.
+// --------------------------------------------------------------------------
+__host__ __device__ inline int tile_coarse_count(const DDGeom &G) {
+    const int full = G.sy / G.c + 1, colc = G.sx / G.c + 1;
+    return full * G.tnx + (G.tny - full) * colc;
+}
+template <class T>
+__host__ __device__ inline size_t tile_record_bytes(const DDGeom &G) {
+    const size_t n = (size_t)tile_coarse_count(G);
+    return ((n * sizeof(T) + 15) & ~(size_t)15) + ((n + 15) & ~(size_t)15);
+}
+// Position of tile node (xl, yl) in the record (-1: not on the coarse set).
+__device__ inline int tile_coarse_index(const DDGeom &G, int xl, int yl) {
+    const int colc = G.sx / G.c + 1;
+    const int full = (yl + G.c - 1) / G.c;  // coarse rows below yl
+    const int base = full * G.tnx + (yl - full) * colc;
+    if (yl % G.c == 0) return base + xl;
+    return xl % G.c == 0 ? base + xl / G.c : -1;
+}
+// Copy slot of tile node (xl, yl) at fine node (X, Y) (as written by Step 3).
+__device__ inline int tile_copy_slot(const DDGeom &G, int xl, int yl, int X, int Y) {
+    int slot = 0;
+    if (X % G.sx == 0 && X > 0 && X < G.nx - 1 && xl == 0) slot |= 1;
+    if (Y % G.sy == 0 && Y > 0 && Y < G.ny - 1 && yl == 0) slot |= 2;
+    return slot;
+}
+
+// pack = 1: copies of tiles [t0, t1) -> their records; pack = 0: every record
+// of tiles [t0, t1) -> the copies.
+template <class T>
+__global__ void k_shard_records(DDArgs<T> A, int t0, int t1, unsigned char *xbuf, int pack) {
+    const DDGeom &G = A.G;
+    const int ncs = tile_coarse_count(G);
+    const size_t rec = tile_record_bytes<T>(G);
+    const size_t voff = ((size_t)ncs * sizeof(T) + 15) & ~(size_t)15;
+    const size_t per_tile = (size_t)G.tnx * G.tny;
+    const size_t total = per_tile * (size_t)(t1 - t0);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int tile = t0 + (int)(e / per_tile);
+        const int rem = (int)(e % per_tile);
+        const int xl = rem % G.tnx, yl = rem / G.tnx;
+        const int idx = tile_coarse_index(G, xl, yl);
+        if (idx < 0) continue;
+        const int X = (tile % G.tx) * G.sx + xl, Y = (tile / G.tx) * G.sy + yl;
+        const size_t slot = (size_t)tile_copy_slot(G, xl, yl, X, Y) * G.coarse_elems + coarse_addr(G, X, Y);
+        unsigned char *r = xbuf + (size_t)tile * rec;
+        T *rv = reinterpret_cast<T *>(r);
+        uint8_t *rw = r + voff;
+        if (pack) {
+            rv[idx] = A.cu[slot];
+            rw[idx] = A.cw[slot];
+        } else {
+            A.cu[slot] = rv[idx];
+            A.cw[slot] = rw[idx];
+        }
     }
 }
 

@@ -48,7 +48,16 @@ EIK_SPIN_LIMIT_SETTER(set_spin_limit_dd)
 EIK_KERNEL_PAIR(k_step1, 96, 168)
 EIK_KERNEL_PAIR(k_step4, 160, 168)
 EIK_KERNEL_PAIR(k_step4a, 160, 168)
-EIK_KERNEL_PAIR(k_fine, 96, 168)
+
+// Subdomain kernel: CTA b solves subdomain A.tile0 + b.
+__global__ void __maxnreg__(96) k_fine_f32(DDArgs<float> A) {
+    extern __shared__ __align__(16) char smem[];
+    k_fine_body<float>(A, smem, A.tile0 + blockIdx.x);
+}
+__global__ void __maxnreg__(168) k_fine_f64(DDArgs<double> A) {
+    extern __shared__ __align__(16) char smem[];
+    k_fine_body<double>(A, smem, A.tile0 + blockIdx.x);
+}
 
 template <class T> struct DDKernels;
 template <> struct DDKernels<float> {
@@ -139,100 +148,157 @@ bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
     return valid_adaptive(p);
 }
 
+// One 2-D DD solve on one stream, in phases: set-up, start (statistics, packed
+// statics, Step 1 and its causal sweep), the subdomain solves of a range of
+// subdomains (Steps 2-3), the coarse phase of an iteration (Alg. 4, the stop
+// test, Step 4, the causal sweep, the update size) and the statistics.  The
+// single solve runs them back to back; a sharded solve runs the subdomain
+// phase on its own subdomains only and exchanges their copies in between.
 template <class T>
-static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
-                  const eik_dd_params *p, void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s) {
-    DDPlan P = dd_plan(grid, p);
+struct DDSolve {
+    DDPlan P;
     DDArgs<T> A;
-    memset(&A, 0, sizeof(A));
-    A.G = P.G;
-    A.r = static_cast<const T *>(r);
-    A.gamma = gamma;
-    A.g = static_cast<const T *>(g);
-    A.u_out = static_cast<T *>(u_out);
-    A.sy = grid->stride[1];
-    dd_layout<T>(P, &A, ws, p->max_iter);
-    A.theta = (T)p->theta;
-    A.step4_identity = (!P.adaptive && p->theta == 0.0) ? 1 : 0;
-    A.tol = (T)p->tol;
-    A.max_iter = p->max_iter;
-    A.max_fsm = p->max_fsm_sweeps;
-    A.max_coarse = p->max_coarse_sweeps;
-    A.adaptive = P.adaptive ? 1 : 0;
-    for (int s2 = 0; s2 < 3; ++s2) A.om[s2] = p->omega[s2];
-    A.sg = p->sig_gamma;
-    A.sd = p->sig_delta;
-    A.sx0 = p->sig_x0;
-    A.cap = p->theta_cap;
-    const DDGeom &G = P.G;
-    const int ntiles = G.tx * G.ty;
-
-    int rc;
-    int dev;
-    if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
-    int nsm = 0;
-    if ((rc = cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr"))) return rc;
-    int smem_optin = 0;
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    auto finek = DDKernels<T>::fine;
-    const int fine_threads = 32 * G.tnb;
-    const size_t fine_smem = P.fine_smem;
-    if ((int)fine_smem > smem_optin || (int)P.step1_smem > smem_optin || (int)P.step4_smem > smem_optin) {
-        set_error("shared memory need (%zu, %zu, %zu) exceeds the device limit %d", fine_smem, P.step1_smem,
-                  P.step4_smem, smem_optin);
-        return EIK_EUNSUPPORTED;
-    }
-    if ((rc = cuda_check(cudaFuncSetAttribute(finek, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fine_smem),
-                         "smem attr fine")))
-        return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.step1_smem),
-                         "smem attr step1")))
-        return rc;
-    auto step4k = P.adaptive ? DDKernels<T>::step4a : DDKernels<T>::step4;
-    if ((rc = cuda_check(cudaFuncSetAttribute(step4k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.step4_smem),
-                         "smem attr step4")))
-        return rc;
-    // causal sweep: cooperative grid sized to what is co-resident
     CausalShape cs;
-    if ((rc = causal_shape<T>((const void *)k_causal<T>, std::max(G.nx, G.ny), std::max(G.ncx, G.ncy) + 1, nsm,
-                              smem_optin, cs)))
-        return rc;
+    cudaStream_t s = nullptr;
+    int nsm = 0, ew = 256, eb = 0, tb = 0, ntiles = 0, fine_threads = 0;
+    size_t fine_smem = 0;
+    void (*step4k)(DDArgs<T>) = nullptr;
+    long long nl = 0;  // launches made
 
-    const int ew = 256;
-    const int eb = (int)std::min<size_t>((G.coarse_elems + ew - 1) / ew, (size_t)nsm * 8);
-    const size_t tiles_nodes = (size_t)ntiles * G.tnx * G.tny;
-    const int tb = (int)std::min<size_t>((tiles_nodes + ew - 1) / ew, (size_t)nsm * 16);
+    int setup(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, const eik_dd_params *p,
+              void *u_out, void *ws, cudaStream_t stream) {
+        s = stream;
+        P = dd_plan(grid, p);
+        memset(&A, 0, sizeof(A));
+        A.G = P.G;
+        A.r = static_cast<const T *>(r);
+        A.gamma = gamma;
+        A.g = static_cast<const T *>(g);
+        A.u_out = static_cast<T *>(u_out);
+        A.sy = grid->stride[1];
+        dd_layout<T>(P, &A, ws, p->max_iter);
+        A.theta = (T)p->theta;
+        A.step4_identity = (!P.adaptive && p->theta == 0.0) ? 1 : 0;
+        A.tol = (T)p->tol;
+        A.max_iter = p->max_iter;
+        A.max_fsm = p->max_fsm_sweeps;
+        A.max_coarse = p->max_coarse_sweeps;
+        A.adaptive = P.adaptive ? 1 : 0;
+        for (int s2 = 0; s2 < 3; ++s2) A.om[s2] = p->omega[s2];
+        A.sg = p->sig_gamma;
+        A.sd = p->sig_delta;
+        A.sx0 = p->sig_x0;
+        A.cap = p->theta_cap;
+        const DDGeom &G = P.G;
+        ntiles = G.tx * G.ty;
 
-    long long nl = 0;
-    EIK_LAUNCH("dd_init", s, k_init_stats<T><<<1, 256, 0, s>>>(A)); ++nl;
-    EIK_LAUNCH("dd_pack_tiles", s, k_pack_tiles<T><<<tb, ew, 0, s>>>(A)); ++nl;
-    EIK_LAUNCH("dd_pack_coarse", s, k_pack_coarse<T><<<eb, ew, 0, s>>>(A)); ++nl;
-    EIK_LAUNCH("dd_step1_coarse_fsm", s, DDKernels<T>::step1<<<G.ngrids, P.grid_threads, P.step1_smem, s>>>(A)); ++nl;
-    auto launch_causal = [&](int only) -> int {
-        void *args[] = {&A, &only, &cs.lw};
+        int rc, dev;
+        if ((rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+        if ((rc = cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "attr"))) return rc;
+        int smem_optin = 0;
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        fine_threads = 32 * G.tnb;
+        fine_smem = P.fine_smem;
+        if ((int)fine_smem > smem_optin || (int)P.step1_smem > smem_optin || (int)P.step4_smem > smem_optin) {
+            set_error("shared memory need (%zu, %zu, %zu) exceeds the device limit %d", fine_smem, P.step1_smem,
+                      P.step4_smem, smem_optin);
+            return EIK_EUNSUPPORTED;
+        }
+        if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::fine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)fine_smem), "smem attr fine")))
+            return rc;
+        if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::step1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)P.step1_smem), "smem attr step1")))
+            return rc;
+        step4k = P.adaptive ? DDKernels<T>::step4a : DDKernels<T>::step4;
+        if ((rc = cuda_check(cudaFuncSetAttribute(step4k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)P.step4_smem), "smem attr step4")))
+            return rc;
+        // causal sweep: cooperative grid sized to what is co-resident
+        if ((rc = causal_shape<T>((const void *)k_causal<T>, std::max(G.nx, G.ny), std::max(G.ncx, G.ncy) + 1, nsm,
+                                  smem_optin, cs)))
+            return rc;
+        eb = (int)std::min<size_t>((G.coarse_elems + ew - 1) / ew, (size_t)nsm * 8);
+        const size_t tiles_nodes = (size_t)ntiles * G.tnx * G.tny;
+        tb = (int)std::min<size_t>((tiles_nodes + ew - 1) / ew, (size_t)nsm * 16);
+        return EIK_OK;
+    }
+
+    int causal(int only_if_not_done) {
+        void *args[] = {&A, &only_if_not_done, &cs.lw};
         int tok = prof_begin("dd_causal_sweep", s);
-        int r2 = cuda_check(cudaLaunchCooperativeKernel((void *)k_causal<T>, cs.blocks, cs.threads, args, cs.smem, s),
+        int rc = cuda_check(cudaLaunchCooperativeKernel((void *)k_causal<T>, cs.blocks, cs.threads, args, cs.smem, s),
                             "causal launch");
         prof_end(tok, s);
         ++nl;
-        return r2;
-    };
-    if ((rc = launch_causal(0))) return rc;
-    for (int k = 0; k <= p->max_iter; ++k) {
-        EIK_LAUNCH("dd_fine_subdomains", s, finek<<<ntiles, fine_threads, fine_smem, s>>>(A)); ++nl;
+        return rc;
+    }
+
+    int start() {
+        const DDGeom &G = P.G;
+        EIK_LAUNCH("dd_init", s, k_init_stats<T><<<1, 256, 0, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd_pack_tiles", s, k_pack_tiles<T><<<tb, ew, 0, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd_pack_coarse", s, k_pack_coarse<T><<<eb, ew, 0, s>>>(A)); ++nl;
+        EIK_LAUNCH("dd_step1_coarse_fsm", s, DDKernels<T>::step1<<<G.ngrids, P.grid_threads, P.step1_smem, s>>>(A));
+        ++nl;
+        return causal(0);
+    }
+
+    // Steps 2-3 on subdomains [t0, t1)
+    int fine(int t0, int t1) {
+        if (t1 <= t0) return EIK_OK;
+        DDArgs<T> B = A;
+        B.tile0 = t0;
+        EIK_LAUNCH("dd_fine_subdomains", s, DDKernels<T>::fine<<<t1 - t0, fine_threads, fine_smem, s>>>(B)); ++nl;
+        return EIK_OK;
+    }
+
+    // copies of subdomains [t0, t1) to (pack) or from (unpack) their records
+    int records(int t0, int t1, void *xbuf, int pack) {
+        if (t1 <= t0) return EIK_OK;
+        const size_t nodes = (size_t)(t1 - t0) * P.G.tnx * P.G.tny;
+        const int nb = (int)std::min<size_t>((nodes + ew - 1) / ew, (size_t)nsm * 16);
+        EIK_LAUNCH(pack ? "dd_shard_pack" : "dd_shard_unpack", s,
+                   k_shard_records<T><<<nb, ew, 0, s>>>(A, t0, t1, static_cast<unsigned char *>(xbuf), pack));
+        ++nl;
+        return EIK_OK;
+    }
+
+    // Alg. 4 and the stop test of iteration k, then (k < max_iter) Step 4, the
+    // causal sweep and the size of the coarse update
+    int coarse(int k) {
         EIK_LAUNCH("dd_alg4_restrict", s, k_alg4<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
         EIK_LAUNCH("dd_check", s, k_check<T><<<1, 1, 0, s>>>(A, k)); ++nl;
-        if (k == p->max_iter) break;
+        if (k == A.max_iter) return EIK_OK;
         if (!A.step4_identity) {
-            EIK_LAUNCH("dd_step4_weighted", s, step4k<<<G.ngrids, P.grid_threads, P.step4_smem, s>>>(A));
+            EIK_LAUNCH("dd_step4_weighted", s, step4k<<<P.G.ngrids, P.grid_threads, P.step4_smem, s>>>(A));
             ++nl;
         }
-        if ((rc = launch_causal(1))) return rc;
+        int rc = causal(1);
+        if (rc) return rc;
         EIK_LAUNCH("dd_delta", s, k_delta<T><<<eb, ew, 0, s>>>(A, k)); ++nl;
+        return EIK_OK;
     }
-    ++nl;
-    EIK_LAUNCH("dd_finalize", s, k_finalize<T><<<1, 32, 0, s>>>(A, stats, nl));
-    return cuda_check(cudaGetLastError(), "dd launch");
+
+    int finish(eik_dd_stats *stats) {
+        ++nl;
+        EIK_LAUNCH("dd_finalize", s, k_finalize<T><<<1, 32, 0, s>>>(A, stats, nl));
+        return cuda_check(cudaGetLastError(), "dd launch");
+    }
+};
+
+template <class T>
+static int dd_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                  const eik_dd_params *p, void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s) {
+    DDSolve<T> D;
+    int rc = D.setup(grid, r, gamma, g, p, u_out, ws, s);
+    if (!rc) rc = D.start();
+    for (int k = 0; !rc && k <= p->max_iter; ++k) {
+        rc = D.fine(0, D.ntiles);
+        if (!rc) rc = D.coarse(k);
+    }
+    if (rc) return rc;
+    return D.finish(stats);
 }
 
 }  // namespace eik
@@ -266,6 +332,122 @@ extern "C" int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *
     if (grid->ndim == 3) return dd3_run(grid, r, gamma, g, params, u_out, ws, stats, s);
     if (grid->dtype == EIK_F64) return dd_run<double>(grid, r, gamma, g, params, u_out, ws, stats, s);
     return dd_run<float>(grid, r, gamma, g, params, u_out, ws, stats, s);
+}
+
+// --------------------------------------------------------------------------
+// Sharded 2-D solve: phases of eik_dd_solve for callers that split the
+// subdomain solves over several processes (slabs of subdomain rows) and keep
+// the coarse state replicated.
+// --------------------------------------------------------------------------
+namespace eik {
+
+static int shard_check(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                       const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes) {
+    if (!dd_validate(grid, params)) return EIK_EINVAL;
+    if (grid->ndim != 2) {
+        set_error("the sharded solve is built for 2-D grids");
+        return EIK_EUNSUPPORTED;
+    }
+    if (!r || !gamma || !g || !u_out || !ws) {
+        set_error("NULL array argument");
+        return EIK_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) & 255) {
+        set_error("workspace must be 256-byte aligned");
+        return EIK_EINVAL;
+    }
+    const size_t need = dd_plan(grid, params).bytes;
+    if (ws_bytes < need) {
+        set_error("workspace of %zu bytes is smaller than the %zu required", ws_bytes, need);
+        return EIK_ENOMEM;
+    }
+    return EIK_OK;
+}
+
+template <class T>
+static int shard_phase(int phase, const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                       const eik_dd_params *p, void *u_out, void *ws, int a, int b, void *xbuf,
+                       eik_dd_stats *stats, cudaStream_t s) {
+    DDSolve<T> D;
+    int rc = D.setup(grid, r, gamma, g, p, u_out, ws, s);
+    if (rc) return rc;
+    const int tx = D.P.G.tx;
+    switch (phase) {
+        case 0: rc = D.start(); break;
+        case 1:  // Steps 2-3 on subdomain rows [a, b), their copies into their records
+            rc = D.fine(a * tx, b * tx);
+            if (!rc) rc = D.records(a * tx, b * tx, xbuf, 1);
+            break;
+        default:  // every record into the copies, then the coarse phase of iteration a
+            rc = D.records(0, D.ntiles, xbuf, 0);
+            if (!rc) rc = D.coarse(a);
+            if (!rc && stats) rc = D.finish(stats);
+            break;
+    }
+    if (rc) return rc;
+    return cuda_check(cudaGetLastError(), "dd shard launch");
+}
+
+static int shard_dispatch(int phase, const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                          const eik_dd_params *p, void *u_out, void *ws, int a, int b, void *xbuf,
+                          eik_dd_stats *stats, void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grid->dtype == EIK_F64) return shard_phase<double>(phase, grid, r, gamma, g, p, u_out, ws, a, b, xbuf, stats, s);
+    return shard_phase<float>(phase, grid, r, gamma, g, p, u_out, ws, a, b, xbuf, stats, s);
+}
+
+}  // namespace eik
+
+extern "C" size_t eik_dd_shard_exchange_bytes(const eik_grid *grid, const eik_dd_params *params,
+                                              size_t *record_bytes) {
+    if (!dd_validate(grid, params)) return 0;
+    if (grid->ndim != 2) {
+        set_error("the sharded solve is built for 2-D grids");
+        return 0;
+    }
+    const DDGeom G = dd_plan(grid, params).G;
+    const size_t rec = grid->dtype == EIK_F64 ? tile_record_bytes<double>(G) : tile_record_bytes<float>(G);
+    if (record_bytes) *record_bytes = rec;
+    return rec * (size_t)G.tx * G.ty;
+}
+
+extern "C" int eik_dd_shard_start(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                                  const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes, void *stream) {
+    int rc = shard_check(grid, r, gamma, g, params, u_out, ws, ws_bytes);
+    if (rc) return rc;
+    return shard_dispatch(0, grid, r, gamma, g, params, u_out, ws, 0, 0, nullptr, nullptr, stream);
+}
+
+extern "C" int eik_dd_shard_fine(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                                 const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes, int row0,
+                                 int row1, void *xbuf, void *stream) {
+    int rc = shard_check(grid, r, gamma, g, params, u_out, ws, ws_bytes);
+    if (rc) return rc;
+    if (row0 < 0 || row1 < row0 || row1 > params->tiles[1]) {
+        set_error("subdomain rows [%d, %d) outside [0, %d]", row0, row1, params->tiles[1]);
+        return EIK_EINVAL;
+    }
+    if (!xbuf || (reinterpret_cast<uintptr_t>(xbuf) & 15)) {
+        set_error("exchange buffer must be non-NULL and 16-byte aligned");
+        return EIK_EINVAL;
+    }
+    return shard_dispatch(1, grid, r, gamma, g, params, u_out, ws, row0, row1, xbuf, nullptr, stream);
+}
+
+extern "C" int eik_dd_shard_coarse(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
+                                   const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes, int k,
+                                   const void *xbuf, eik_dd_stats *stats, void *stream) {
+    int rc = shard_check(grid, r, gamma, g, params, u_out, ws, ws_bytes);
+    if (rc) return rc;
+    if (k < 0 || k > params->max_iter) {
+        set_error("iteration %d outside [0, max_iter = %d]", k, params->max_iter);
+        return EIK_EINVAL;
+    }
+    if (!xbuf || (reinterpret_cast<uintptr_t>(xbuf) & 15)) {
+        set_error("exchange buffer must be non-NULL and 16-byte aligned");
+        return EIK_EINVAL;
+    }
+    return shard_dispatch(2, grid, r, gamma, g, params, u_out, ws, k, 0, const_cast<void *>(xbuf), stats, stream);
 }
 
 // --------------------------------------------------------------------------

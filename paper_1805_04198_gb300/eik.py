@@ -8,7 +8,8 @@ Entry points mirror the C names:
     eik_fsm_workspace_size, eik_fsm, eik_dd_workspace_size, eik_dd_solve,
     eik_dd_batched_workspace_size, eik_dd_solve_batched, eik_dd_batched_autotune,
     eik_fsm_many_workspace_size, eik_fsm_many, eik_dd_adjoint_many_workspace_size,
-    eik_dd_adjoint_many, eik_set_wait_limit, eik_last_error, eik_version
+    eik_dd_adjoint_many, eik_dd_shard_exchange_bytes, eik_dd_shard_start, eik_dd_shard_fine,
+    eik_dd_shard_coarse, eik_set_wait_limit, eik_last_error, eik_version
 plus the conveniences :func:`fsm` and :func:`dd_solve`, which allocate the
 workspace and the output with torch and return host-side statistics.
 """
@@ -130,6 +131,18 @@ def load():
         lib.eik_dd_adjoint_many.restype = ctypes.c_int
         lib.eik_dd_adjoint_many.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, vp, pp, pp, pp, pp, vp,
                                             ctypes.c_int64, vp, ctypes.c_size_t, vp, vp]
+        lib.eik_dd_shard_exchange_bytes.restype = ctypes.c_size_t
+        lib.eik_dd_shard_exchange_bytes.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(DDParams),
+                                                    ctypes.POINTER(ctypes.c_size_t)]
+        lib.eik_dd_shard_start.restype = ctypes.c_int
+        lib.eik_dd_shard_start.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp,
+                                           ctypes.c_size_t, vp]
+        lib.eik_dd_shard_fine.restype = ctypes.c_int
+        lib.eik_dd_shard_fine.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp,
+                                          ctypes.c_size_t, ctypes.c_int, ctypes.c_int, vp, vp]
+        lib.eik_dd_shard_coarse.restype = ctypes.c_int
+        lib.eik_dd_shard_coarse.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp,
+                                            ctypes.c_size_t, ctypes.c_int, vp, vp, vp]
         lib.eik_set_wait_limit.restype = ctypes.c_int
         lib.eik_set_wait_limit.argtypes = [ctypes.c_int64]
         lib.eik_profile_enable.restype = ctypes.c_int
@@ -146,6 +159,33 @@ def eik_last_error() -> str:
 
 def eik_version() -> int:
     return load().eik_version()
+
+
+def eik_dd_shard_exchange_bytes(grid: Grid, params: DDParams):
+    """(bytes of the exchange buffer, bytes of one subdomain's record)."""
+    rec = ctypes.c_size_t(0)
+    n = int(load().eik_dd_shard_exchange_bytes(ctypes.byref(grid), ctypes.byref(params), ctypes.byref(rec)))
+    if n == 0:
+        raise EikError(-1, eik_last_error())
+    return n, int(rec.value)
+
+
+def eik_dd_shard_start(grid, r, gamma, g, params, u_out, ws, stream=None):
+    wsp, wsn = _aligned(ws)
+    _check(load().eik_dd_shard_start(ctypes.byref(grid), _ptr(r), _ptr(gamma), _ptr(g), ctypes.byref(params),
+                                     _ptr(u_out), wsp, wsn, _stream(stream)))
+
+
+def eik_dd_shard_fine(grid, r, gamma, g, params, u_out, ws, row0, row1, xbuf, stream=None):
+    wsp, wsn = _aligned(ws)
+    _check(load().eik_dd_shard_fine(ctypes.byref(grid), _ptr(r), _ptr(gamma), _ptr(g), ctypes.byref(params),
+                                    _ptr(u_out), wsp, wsn, int(row0), int(row1), _ptr(xbuf), _stream(stream)))
+
+
+def eik_dd_shard_coarse(grid, r, gamma, g, params, u_out, ws, k, xbuf, stats_dev, stream=None):
+    wsp, wsn = _aligned(ws)
+    _check(load().eik_dd_shard_coarse(ctypes.byref(grid), _ptr(r), _ptr(gamma), _ptr(g), ctypes.byref(params),
+                                      _ptr(u_out), wsp, wsn, int(k), _ptr(xbuf), _ptr(stats_dev), _stream(stream)))
 
 
 def eik_set_wait_limit(iterations: int) -> None:
