@@ -791,24 +791,35 @@ def run_extra(args):
         data = ut.reshape(S, -1)[:, rec].clone()
         del ut
 
-        def gradient():
-            # all sources in one forward (eik_fsm_many) and one backward
-            # (eik_dd_adjoint_many, gradients summed in the library)
+        # the forward of every source by the DD as configured (16 x 16
+        # subdomains, coarse ratio 8, weight 0, stop at a coarse update below
+        # 1e-6): one batched solve over the sources, built once for R
+        many_dd = eik.ManyDD(R, gams, gz, h, (16, 16), 8, theta=0.0, max_iter=42, tol=TOL,
+                             max_coarse_sweeps=MAX_COARSE_SWEEPS)
+
+        def gradient(dd=many_dd):
+            # all sources in one forward (the batched DD, or eik_fsm_many) and
+            # one backward (eik_dd_adjoint_many, gradients summed in the library)
             rr = R.detach().requires_grad_(True)
-            u = eik.EikonalSolveMany.apply(rr, gams, gz, h)
+            u = eik.EikonalSolveMany.apply(rr, gams, gz, h, dd)
             L = 0.5 * ((u.reshape(S, -1)[:, rec] - data) ** 2).sum()
             L.backward()
             return rr.grad
         prof = _profiled(torch, eik, gradient)
         with ClockSampler(local_rank) as clk:
             ms = _timed(torch, gradient, args.steps, args.warmup, flush, stream)
-        fs = prof.get("fsm_sweeps", {"total_ms": float("nan")})
+        fs = prof.get("dd_batch_fine_subdomains", prof.get("dd_fine_subdomains", {"total_ms": float("nan")}))
+        fine_name = "dd_batch_fine_subdomains" if "dd_batch_fine_subdomains" in prof else "dd_fine_subdomains"
+        ms_fsm_fwd = _timed(torch, lambda: gradient(None), args.steps, args.warmup, flush, stream)
+        dst = many_dd.stats()
         extra = {"kernel_ms": {k: v["total_ms"] for k, v in prof.items()}, "sources": S,
-                 "receivers": len(w["rec_rows"])}
-        # sweeps of every source for the algorithmic byte count of the forward kernel
-        _, fsts = eik.fsm_many(R, gams, gz, h)
-        fwd_upd = sum(x["updates"] for x in fsts)
-        kern = ("fsm_sweeps", fwd_upd * BYTES_PER_UPDATE_F32 / (fs["total_ms"] / 1e3) / 1e9)
+                 "receivers": len(w["rec_rows"]),
+                 "dd_forward": {"iters_max": max(x["iters"] for x in dst),
+                                "converged": sum(x["converged"] for x in dst)},
+                 "fsm_forward_ms_per_step": ms_fsm_fwd}
+        # fine updates of every source for the algorithmic byte count of the subdomain kernel
+        fwd_upd = sum(x["fine_updates"] for x in dst)
+        kern = (fine_name, fwd_upd * BYTES_PER_UPDATE_F32 / (fs["total_ms"] / 1e3) / 1e9)
         hr = torch.from_numpy(w["r0"].astype(np.float32)).pin_memory()
         hg = torch.empty_like(hr).pin_memory()
         def e2e_step():
@@ -819,20 +830,24 @@ def run_extra(args):
         e2e = {"value": S / (e2e_ms / 1e3), "unit": "sources/s", "h2d_bytes_per_step": hr.numel() * 4,
                "d2h_bytes_per_step": hg.numel() * 4, "ms_per_step": e2e_ms}
         workload = {"workload": "tomography_1025_64src_256rec", "n": n, "sources": 64, "receivers": 256,
-                    "forward": "fsm, all sources in one call",  "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
+                    "forward": "DD (16 x 16 subdomains, coarse ratio 8, weight 0, stop at 1e-6), all sources in one "
+                               "batched solve; the u of the converged solve is the only forward state kept",
+                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
         unit, metric = "sources/s", "travel-time tomography: gradient dL/dr, sources (forward + adjoint) per second"
         if rank == 0 and not args.no_cpu_baseline:
             t0 = time.perf_counter()
             gam = np.zeros((n, n), np.uint8)
             gam[w["src_rows"][0], 0] = 1
             r64 = w["r0"].astype(np.float32).astype(np.float64)
-            u0, _, _ = oracle.fsm(r64, gam, 0.0, h)
+            u0, so, _ = oracle.dd(r64, gam, np.zeros((n, n)), h, (16, 16), 8, theta=0.0, max_iter=42, tol=TOL,
+                                  max_coarse_sweeps=MAX_COARSE_SWEEPS, parallel=True)
             dJ = np.zeros((n, n))
             dJ[w["rec_rows"], n - 1] = 1.0
             oracle.adjoint(r64, gam, u0, dJ, h)
             dt = time.perf_counter() - t0
-            cpu = {"value": 1.0 / dt, "unit": unit, "cores": 1, "kind": "oracle",
-                   "sample": "one source: forward FSM + adjoint, FP64, %.1f s" % dt}
+            cpu = {"value": 1.0 / dt, "unit": unit, "cores": host_cpu()["threads"], "kind": "oracle",
+                   "sample": "one source: forward DD (16 x 16, c = 8, %d iterations, OpenMP) + adjoint "
+                             "(serial), FP64, %.1f s" % (so["iters"], dt)}
         value = S * world / (ms / 1e3)
     if rank == 0:
         line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,

@@ -580,15 +580,45 @@ def adjoint_many(r, gammas, us, dJdus, h, per_problem=False, max_sweeps=100000, 
     return gsum, per, stats
 
 
+class ManyDD:
+    """Forward solve of many source sets on one grid by the two-scale DD
+    (Sec. 3.2): one batched solve (eik_dd_solve_batched) whose problems share
+    the slowness r and differ in gamma and g (stacked [S, ny, nx]).  Built once
+    for r's storage; solve(r) reruns it (the batch holds r's address, so r
+    must be that tensor or a view of the same storage).  Keyword arguments as
+    for dd_params (theta, max_iter, tol, max_coarse_sweeps, ...)."""
+
+    def __init__(self, r, gammas, gs, h, tiles, coarse_ratio, config=None, **params):
+        self.ptr = r.data_ptr()
+        self.shape = tuple(gammas.shape)
+        probs = [dict(r=r, gamma=gammas[s], g=gs[s], h=h, tiles=tiles, coarse_ratio=coarse_ratio, **params)
+                 for s in range(gammas.shape[0])]
+        self.batch = DDBatch(probs, config=config)
+
+    def solve(self, r):
+        if r.data_ptr() != self.ptr:
+            raise ValueError("ManyDD was built for another slowness tensor")
+        self.batch.run()
+        return torch.stack(self.batch.u)
+
+    def stats(self):
+        return self.batch.stats()
+
+
 class EikonalSolveMany(torch.autograd.Function):
     """u[s] = Eikonal solution for slowness r and source set s (2-D), all
     source sets solved together; differentiable in r.  gammas, gs: stacked
-    [S, ny, nx].  backward sums the per-source gradients in the library
-    (eik_dd_adjoint_many), keeping only the forward u."""
+    [S, ny, nx].  The forward is the plain FSM of every source in one call
+    (eik_fsm_many), or the DD when `dd` is a ManyDD built for r.  Only the
+    converged u is kept for the backward (no iterate of either solver), which
+    sums the per-source gradients in the library (eik_dd_adjoint_many)."""
 
     @staticmethod
-    def forward(ctx, r, gammas, gs, h):
-        u, _ = fsm_many(r, gammas, gs, h, sync=False)
+    def forward(ctx, r, gammas, gs, h, dd=None):
+        if dd is None:
+            u, _ = fsm_many(r, gammas, gs, h, sync=False)
+        else:
+            u = dd.solve(r)
         ctx.save_for_backward(r, gammas, u)
         ctx.h = h
         return u
@@ -597,7 +627,7 @@ class EikonalSolveMany(torch.autograd.Function):
     def backward(ctx, grad_u):
         r, gammas, u = ctx.saved_tensors
         gsum, _, _ = adjoint_many(r, gammas, u, grad_u.contiguous(), ctx.h, sync=False)
-        return gsum, None, None, None
+        return gsum, None, None, None, None
 
 
 def parse_dd_stats(st: torch.Tensor) -> dict:
