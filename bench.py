@@ -242,9 +242,10 @@ def main():
     ap.add_argument("--theta", default="0",
                     help="a constant weight (default 0) or 'adaptive' (the per-node weight of Sec. 4.2)")
     ap.add_argument("--workload", default="dd4097",
-                    choices=["dd4097", "batch256", "dd3d257", "tomography1025", "obstacles"],
+                    choices=["dd4097", "batch256", "dd3d257", "tomography1025", "obstacles", "dd1bump"],
                     help="dd4097 (default) is the benchmark line; the others measure the batched solve, the "
-                         "3-D solve and the tomography gradient with the same keys")
+                         "3-D solve, the tomography gradient, the Sec. 4 obstacle fields and the 1-D method "
+                         "with the same keys")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -615,6 +616,64 @@ def run_extra(args):
             cpu = {"value": cu / dt / 1e9, "unit": unit, "cores": 1, "kind": "oracle",
                    "sample": "the first two 257^2 problems of the batch, full solves, %.1f s" % dt}
         value = upd * world / (ms / 1e3) / 1e9
+    elif args.workload == "dd1bump":
+        # the 1-D method (Sec. 3.1) on its example slowness (Gaussian bump at
+        # x = 0.75, u(0) = u(1) = 0), 1024 subintervals of 1000 cells, FP64
+        N, M = 1024, 1000
+        n, h = N * M + 1, 1.0 / (N * M)
+        x = np.arange(n) * h
+        r64 = 1.0 + 10.0 * np.exp(-(x - 0.75) ** 2 / (2 * 0.01 ** 2))
+        gam = np.zeros(n, np.uint8)
+        gam[0] = gam[-1] = 1
+        # theta = 1: the coarse grid (H = 1/1024) resolves the bump, and the
+        # full parareal correction converges in 2 iterations; theta = 0.5
+        # (119 iterations) is timed as an extra field
+        kw = dict(theta=1.0, max_iter=400, tol=1e-12, max_coarse_sweeps=1000)
+        R, G, g = t(r64), t(gam), t(np.zeros(n))
+        grid = eik.make_grid(R, h)
+        params = eik.dd_params((N,), M, **kw)
+        ws = torch.empty(eik.eik_dd_workspace_size(grid, params) + 256, dtype=torch.uint8, device=dev)
+        u = torch.empty_like(R)
+        st_dev = torch.zeros(eik.ctypes.sizeof(eik.DDStats), dtype=torch.uint8, device=dev)
+        solve = lambda: eik.eik_dd_solve(grid, R, G, g, params, u, ws, st_dev, stream)
+        prof = _profiled(torch, eik, solve)
+        with ClockSampler(local_rank) as clk:
+            ms = _timed(torch, solve, args.steps, args.warmup, flush, stream)
+        st = eik.parse_dd_stats(st_dev)
+        upd = st["fine_updates"] + st["coarse_updates"]
+        k_ms = prof["dd1_iteration"]["total_ms"]
+        # FP64: u in, r in, u out per fine update
+        kern = ("dd1_iteration", st["fine_updates"] * 24 / (k_ms / 1e3) / 1e9)
+        p_half = eik.dd_params((N,), M, **dict(kw, theta=0.5))
+        st_half = torch.zeros_like(st_dev)
+        ms_half = _timed(torch, lambda: eik.eik_dd_solve(grid, R, G, g, p_half, u, ws, st_half, stream), 2, 1,
+                         flush, stream)
+        sh = eik.parse_dd_stats(st_half)
+        extra = {"dd_stats": {k: st[k] for k in ("iters", "converged", "fsm_sweeps_max", "coarse_sweeps_max",
+                                                 "causal_rounds_max", "fine_updates", "coarse_updates")},
+                 "theta_0.5": {"ms": ms_half, "iters": sh["iters"], "converged": sh["converged"]},
+                 "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
+                 "note": "one CTA runs the whole iteration (coarse state in shared memory), so the kernel "
+                         "is bound by one SM's latency, not by HBM"}
+        hr = torch.from_numpy(r64).pin_memory()
+        hu = torch.empty_like(hr).pin_memory()
+        def e2e_step():
+            R.copy_(hr, non_blocking=True)
+            solve()
+            hu.copy_(u, non_blocking=True)
+        e2e_ms = _timed(torch, e2e_step, max(1, args.steps // 2), 1, flush, stream)
+        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": hr.numel() * 8,
+               "d2h_bytes_per_step": hu.numel() * 8, "ms_per_step": e2e_ms}
+        workload = {"workload": "dd1_bump_1024001", "N": N, "M": M, "theta": 1.0, "tol": 1e-12,
+                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
+        unit, metric = "ms", "1-D DD (Sec. 3.1) solve to tol 1e-12, milliseconds"
+        if rank == 0 and not args.no_cpu_baseline:
+            t0 = time.perf_counter()
+            _, so, _ = oracle.dd1(r64, gam, 0.0, h, N, M, **kw)
+            dt = time.perf_counter() - t0
+            cpu = {"value": dt * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+                   "sample": "the whole solve, FP64, %d iterations" % so["iters"]}
+        value = ms
     elif args.workload == "dd3d257":
         w = inputs.workload_c2()
         R, G, g = t(w["r"].astype(np.float32)), t(w["gamma"]), t(w["g"].astype(np.float32))
@@ -852,10 +911,12 @@ def run_extra(args):
     if rank == 0:
         line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": unit != "ms", "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload,
+                "vs_baseline": None, "dtype": "f64" if args.workload == "dd1bump" else "f32", "data": "synthetic",
+                "config": workload,
                 "roofline": {"bound": "hbm", "achieved": kern[1], "peak": peak, "unit": "GB/s",
                              "frac": kern[1] / peak, "traffic": None, "kernel": kern[0], "peak_source": peak_kind,
-                             "algorithmic_bytes": "12 B per node update (u in, r in, u out)"},
+                             "algorithmic_bytes": "%d B per node update (u in, r in, u out)" %
+                                                  (24 if args.workload == "dd1bump" else 12)},
                 "gpu_launches": sum(v["launches"] for v in prof.values()) * args.steps, "e2e": e2e,
                 "clocks": clk.summary(), "cpu_baseline": cpu, **extra}
         print(json.dumps(line))

@@ -166,6 +166,17 @@ size_t eik_dd_workspace_size(const eik_grid *grid, const eik_dd_params *params);
  * ws: scratch of eik_dd_workspace_size() bytes, 256-byte aligned, no
  * initialisation needed.  Returns EIK_OK, EIK_EINVAL, EIK_ENOMEM, EIK_ECUDA or
  * EIK_EUNSUPPORTED.
+ *
+ * grid->ndim == 1: the one-dimensional method of Sec. 3.1 (eq. 1d, Steps 1-4)
+ * on n[0] = N M + 1 nodes, N = tiles[0] subintervals (at most 2048) of M
+ * cells; coarse_ratio must equal M (the coarse nodes are the subinterval
+ * ends, H = M h).  C_H is eq. 1dgod; Step 1 is the coarse FSM with no causal
+ * sweep; Step 3 chooses u^k_i between the two end copies by their fine winds;
+ * Step 4 applies the weighted update where W^k = w^k = W~, u^k elsewhere,
+ * then the causal sweep of Sec. 3.1 in both directions until stable.  The
+ * per-node weight (theta_adaptive) is rejected.  The whole iteration runs in
+ * one kernel launch and uses no workspace (eik_dd_workspace_size returns 256
+ * for a valid request; ws must still be a valid 256-byte-aligned pointer).
  */
 int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
                  const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes,

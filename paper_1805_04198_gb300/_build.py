@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libeik.so")
-SOURCES = ["eik_dd.cu", "eik_dd_batch.cu", "eik_dd3.cu", "eik_fsm.cu", "eik_fsm3.cu", "eik_adjoint.cu"]
+SOURCES = ["eik_dd.cu", "eik_dd1.cu", "eik_dd_batch.cu", "eik_dd3.cu", "eik_fsm.cu", "eik_fsm3.cu", "eik_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -81,6 +81,11 @@ size_t dd3_workspace_size(const eik_grid *grid, const eik_dd_params *p);
 bool dd3_validate(const eik_grid *grid, const eik_dd_params *p);
 int dd3_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, const eik_dd_params *p,
             void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s);
+// 1-D implementation (eik_dd1.cu)
+bool dd1_validate(const eik_grid *grid, const eik_dd_params *p);
+size_t dd1_workspace_size();
+int dd1_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, const eik_dd_params *p,
+            void *u_out, eik_dd_stats *stats, cudaStream_t s);
 
 // Parameters of the per-node weight of Sec. 4.2 (2-D and 3-D).
 static bool valid_adaptive(const eik_dd_params *p) {
@@ -100,6 +105,7 @@ bool dd_validate(const eik_grid *grid, const eik_dd_params *p) {
         set_error("params is NULL");
         return false;
     }
+    if (grid && grid->ndim == 1) return dd1_validate(grid, p);
     if (grid && grid->ndim == 3) {
         if (!valid_grid_common(grid, 3)) return false;
         if (p->max_iter < 0 || p->max_iter > 100000 || p->max_fsm_sweeps < 1 || p->max_coarse_sweeps < 1 ||
@@ -307,6 +313,7 @@ using namespace eik;
 
 extern "C" size_t eik_dd_workspace_size(const eik_grid *grid, const eik_dd_params *params) {
     if (!dd_validate(grid, params)) return 0;
+    if (grid->ndim == 1) return dd1_workspace_size();
     if (grid->ndim == 3) return dd3_workspace_size(grid, params);
     return dd_plan(grid, params).bytes;
 }
@@ -323,12 +330,15 @@ extern "C" int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *
         set_error("workspace must be 256-byte aligned");
         return EIK_EINVAL;
     }
-    const size_t need = grid->ndim == 3 ? dd3_workspace_size(grid, params) : dd_plan(grid, params).bytes;
+    const size_t need = grid->ndim == 1   ? dd1_workspace_size()
+                        : grid->ndim == 3 ? dd3_workspace_size(grid, params)
+                                          : dd_plan(grid, params).bytes;
     if (ws_bytes < need) {
         set_error("workspace of %zu bytes is smaller than the %zu required", ws_bytes, need);
         return EIK_ENOMEM;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grid->ndim == 1) return dd1_run(grid, r, gamma, g, params, u_out, stats, s);
     if (grid->ndim == 3) return dd3_run(grid, r, gamma, g, params, u_out, ws, stats, s);
     if (grid->dtype == EIK_F64) return dd_run<double>(grid, r, gamma, g, params, u_out, ws, stats, s);
     return dd_run<float>(grid, r, gamma, g, params, u_out, ws, stats, s);

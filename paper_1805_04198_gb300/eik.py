@@ -200,9 +200,10 @@ def _check(code):
 
 
 def make_grid(t: torch.Tensor, h: float) -> Grid:
-    """eik_grid describing tensor t of shape (ny, nx) or (nz, ny, nx)."""
-    if t.dim() not in (2, 3):
-        raise ValueError("expected a 2-D or 3-D tensor")
+    """eik_grid describing tensor t of shape (nx,) (the 1-D method of
+    eik_dd_solve only), (ny, nx) or (nz, ny, nx)."""
+    if t.dim() not in (1, 2, 3):
+        raise ValueError("expected a 1-D, 2-D or 3-D tensor")
     if t.dtype not in (torch.float32, torch.float64):
         raise ValueError("dtype must be float32 or float64")
     if t.stride(-1) != 1:
@@ -210,6 +211,8 @@ def make_grid(t: torch.Tensor, h: float) -> Grid:
     d = t.dim()
     n = list(reversed(t.shape)) + [1] * (3 - d)
     st = list(reversed(t.stride())) + [0] * (3 - d)
+    if d == 1:
+        st[1] = st[2] = n[0]
     if d == 2:
         st[2] = st[1] * n[1]
     return Grid(d, EIK_F64 if t.dtype == torch.float64 else EIK_F32, (ctypes.c_int64 * 3)(*n),
@@ -323,7 +326,9 @@ def fsm(r, gamma, g, h, max_sweeps=100000, stream=None, sync=True):
 
 def dd_solve(r, gamma, g, h, tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
              max_coarse_sweeps=8, stream=None, sync=True, **adaptive):
-    """Two-scale DD solve (Sec. 3.2).  Returns (u, stats dict).  Keyword
+    """Two-scale DD solve (Sec. 3.2; Sec. 3.1 for a 1-D r, where tiles =
+    (N,) subintervals and coarse_ratio must be their width M).  Returns (u,
+    stats dict).  Keyword
     arguments theta_adaptive, omega, sig_gamma, sig_delta, sig_x0, theta_cap
     select the per-node weight of Sec. 4.2 (see dd_params)."""
     _check_like(r, g)

@@ -78,3 +78,23 @@ def test_noalloc_scratch_size_matches_header(lib):
     m = re.search(r"#define\s+EIK_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", hdr)
     assert m, "EIK_NOALLOC_SCRATCH_BYTES not found in eik.h"
     assert lib.NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+
+
+def test_one_dimensional_requests(lib):
+    """1-D grids go to the Sec. 3.1 solve: a valid request needs 256 bytes
+    (no workspace); coarse_ratio must be the subinterval width, at most 2048
+    subintervals, no per-node weight; the other entry points reject 1-D."""
+    g = lib.Grid(1, 1, (ctypes.c_int64 * 3)(1001, 1, 1), (ctypes.c_int64 * 3)(1, 1001, 1001), 1e-3)
+    assert lib.eik_dd_workspace_size(g, lib.dd_params((10,), 100)) == 256
+    assert lib.eik_dd_workspace_size(g, lib.dd_params((10,), 50)) == 0
+    assert "coarse_ratio" in lib.eik_last_error()
+    assert lib.eik_dd_workspace_size(g, lib.dd_params((7,), 100)) == 0
+    assert lib.eik_dd_workspace_size(g, lib.dd_params((10,), 100, theta_adaptive=True)) == 0
+    big = lib.Grid(1, 0, (ctypes.c_int64 * 3)(2049 * 2 + 1, 1, 1), (ctypes.c_int64 * 3)(1, 1, 1), 1e-3)
+    assert lib.eik_dd_workspace_size(big, lib.dd_params((2049,), 2)) == 0
+    assert "2048" in lib.eik_last_error()
+    ok = lib.Grid(1, 0, (ctypes.c_int64 * 3)(2048 * 2 + 1, 1, 1), (ctypes.c_int64 * 3)(1, 1, 1), 1e-3)
+    assert lib.eik_dd_workspace_size(ok, lib.dd_params((2048,), 2)) == 256
+    assert lib.eik_fsm_workspace_size(g) == 0
+    with pytest.raises(lib.EikError, match="2-D"):
+        lib.eik_dd_shard_exchange_bytes(g, lib.dd_params((10,), 100))
