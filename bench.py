@@ -653,8 +653,9 @@ def run_extra(args):
                                                  "causal_rounds_max", "fine_updates", "coarse_updates")},
                  "theta_0.5": {"ms": ms_half, "iters": sh["iters"], "converged": sh["converged"]},
                  "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
-                 "note": "one CTA runs the whole iteration (coarse state in shared memory), so the kernel "
-                         "is bound by one SM's latency, not by HBM"}
+                 "note": "one cooperative launch: one thread per subinterval (a chain of dependent "
+                         "updates), the serial coarse work on one thread of CTA 0, so the kernel is bound by "
+                         "latency, not by HBM"}
         hr = torch.from_numpy(r64).pin_memory()
         hu = torch.empty_like(hr).pin_memory()
         def e2e_step():

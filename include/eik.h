@@ -45,8 +45,9 @@ typedef enum {
     EIK_EUNSUPPORTED = -5     /* valid request this build does not implement */
 } eik_status;
 
-/* Grid description.  ndim = 2 or 3; n[a] = number of nodes along axis a
- * (n[2] = 1 when ndim = 2); h = node spacing (same on every axis). */
+/* Grid description.  ndim = 2 or 3 (1 for eik_dd_solve's one-dimensional
+ * method only); n[a] = number of nodes along axis a (n[a] = 1 beyond ndim);
+ * h = node spacing (same on every axis). */
 typedef struct {
     int ndim;
     int dtype;          /* eik_dtype */
@@ -141,6 +142,10 @@ typedef struct {
     int64_t fine_updates;  /* Godunov local solves executed in the subdomains (Step 3) */
     int64_t coarse_updates;/* local solves executed on the coarse grids (Steps 1, 4) */
     int64_t launches;      /* kernels enqueued by this call */
+    int64_t fine_solves_skipped; /* subdomain solves (Step 3) not repeated because the
+                                    subdomain's Step 2 data equal those of its previous
+                                    solve in this call (its results are kept: the same
+                                    solve gives them bit for bit); 2-D solves */
 } eik_dd_stats;
 
 /* Workspace (bytes, device) needed by eik_dd_solve; 0 if the request is invalid. */
@@ -175,8 +180,10 @@ size_t eik_dd_workspace_size(const eik_grid *grid, const eik_dd_params *params);
  * Step 4 applies the weighted update where W^k = w^k = W~, u^k elsewhere,
  * then the causal sweep of Sec. 3.1 in both directions until stable.  The
  * per-node weight (theta_adaptive) is rejected.  The whole iteration runs in
- * one kernel launch and uses no workspace (eik_dd_workspace_size returns 256
- * for a valid request; ws must still be a valid 256-byte-aligned pointer).
+ * one cooperative kernel launch (the subintervals spread over one CTA per SM,
+ * the coarse state in CTA 0's shared memory, bounded grid barriers between
+ * the phases); the workspace holds a few control words, U and W, and the
+ * subintervals' end copies (a few kB).
  */
 int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g,
                  const eik_dd_params *params, void *u_out, void *ws, size_t ws_bytes,
@@ -201,9 +208,10 @@ int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, cons
  *                       of iteration k, then (k < max_iter) Step 4, the causal
  *                       sweep and the update size; statistics into stats
  *                       (device) as eik_dd_solve writes them, except that
- *                       fine_updates, fsm_sweeps_max and fsm_cap_hits count
- *                       this process's subdomains (sum, max and sum over the
- *                       processes give eik_dd_solve's).  The iteration stops
+ *                       fine_updates, fsm_sweeps_max, fsm_cap_hits and
+ *                       fine_solves_skipped count this process's subdomains
+ *                       (sum, max, sum and sum over the processes give
+ *                       eik_dd_solve's).  The iteration stops
  *                       after k when stats.converged, stats.error or
  *                       k == max_iter.
  * eik_dd_shard_start (set-up, Step 1 and its causal sweep) runs once before.

@@ -165,8 +165,10 @@ __device__ __forceinline__ long long spin_limit() { return *(volatile const long
 // Grid-wide barrier for cooperative launches (all CTAs co-resident).  bar[0]
 // counts arrivals, bar[1] is the generation.  The wait is bounded by `lim`
 // polls (the kernel reads spin_limit() once when it starts): on timeout the
-// error word is set and false is returned (the caller then returns).
+// error word is set and false is returned to every thread of the CTA (the
+// caller then returns with the whole CTA).
 __device__ inline bool grid_barrier(unsigned *bar, int *err, long long lim) {
+    __shared__ int s_barrier_ok;
     __syncthreads();
     bool ok = true;
     if (threadIdx.x == 0) {
@@ -190,8 +192,11 @@ __device__ inline bool grid_barrier(unsigned *bar, int *err, long long lim) {
             }
         }
         __threadfence();
+        s_barrier_ok = ok ? 1 : 0;
     }
     __syncthreads();
+    ok = s_barrier_ok != 0;
+    __syncthreads();  // s_barrier_ok is read by all before the next barrier writes it
     return ok;
 }
 

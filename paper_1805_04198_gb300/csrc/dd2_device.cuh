@@ -13,7 +13,7 @@ namespace eik {
 
 struct DevStats {
     unsigned long long fsm_sweeps_max, coarse_sweeps_max, fsm_caps, coarse_caps;
-    unsigned long long fine_updates, coarse_updates;
+    unsigned long long fine_updates, coarse_updates, fine_skips;
     int causal_rounds_max;
     int err;
     int iters;
@@ -48,6 +48,13 @@ struct DDArgs {
     int *ldirty;     // [ncy+1] horizontal then [ncx+1] vertical coarse lines the causal sweep must
                      // (re)visit; null: every line in every round
     int tile0;       // first subdomain of a subdomain launch (a slab of a sharded solve)
+    // Step 2 data of each subdomain's last solve in this call, for the skip of
+    // a solve whose data are unchanged: per face node the starting value and
+    // the coarse wind an inflow copy echoes ([ntiles][face_nodes]); sig_ok
+    // [ntiles] = 1 once the subdomain has been solved in this call
+    T *sig_u;
+    uint8_t *sig_w;
+    int *sig_ok;
     unsigned *bar;   // [2] grid barrier count / generation
     DevStats *st;
     T theta, tol;
@@ -534,9 +541,75 @@ __device__ __forceinline__ bool tile_inflow(const DDArgs<T> &A, int xl, int yl, 
     return (xl == 0 && wx > 0) || (xl == G.sx && wx < 0) || (yl == 0 && wy > 0) || (yl == G.sy && wy < 0);
 }
 
+// Face nodes of a subdomain box (NX x NY nodes): the bottom and top rows,
+// then the left and right columns without their corners.
+__host__ __device__ inline int tile_face_count(const DDGeom &G) { return 2 * G.tnx + 2 * (G.tny - 2); }
+__device__ inline void tile_face_node(const DDGeom &G, int f, int &xl, int &yl) {
+    const int NX = G.tnx, NY = G.tny;
+    if (f < NX) { xl = f; yl = 0; }
+    else if (f < 2 * NX) { xl = f - NX; yl = NY - 1; }
+    else if (f < 2 * NX + NY - 2) { xl = 0; yl = 1 + f - 2 * NX; }
+    else { xl = NX - 1; yl = 1 + f - 2 * NX - (NY - 2); }
+}
+
+template <class T>
+__device__ __forceinline__ bool same_bits(T a, T b);
+template <>
+__device__ __forceinline__ bool same_bits<float>(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+template <>
+__device__ __forceinline__ bool same_bits<double>(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+// Whether subdomain `tile` must be solved in this iteration: its Step 2 data
+// (every face node's starting value, and the coarse wind that an inflow node
+// keeping its value echoes in Step 3's copies) differ from those of its last
+// solve in this call, or it has not been solved yet.  The interior starts at
+// +inf and r, Gamma and g do not change within a call, so equal data give the
+// same solve bit for bit: its results (the fine values in u_out, the copies at
+// the coarse-set nodes, the subdomain state) are still in place.  Records the
+// new data.  All threads of the CTA call it and get the same answer.
+template <class T>
+__device__ bool tile_needs_solve(const DDArgs<T> &A, int tile) {
+    const DDGeom &G = A.G;
+    const T INF = Num<T>::inf();
+    const int tx = tile % G.tx, ty = tile / G.tx;
+    const int nf = tile_face_count(G);
+    T *su = A.sig_u + (size_t)tile * nf;
+    uint8_t *sw = A.sig_w + (size_t)tile * nf;
+    bool diff = false;
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+        int xl, yl;
+        tile_face_node(G, f, xl, yl);
+        const int X = tx * G.sx + xl, Y = ty * G.sy + yl;
+        T v = INF;
+        uint8_t wv = 0;
+        size_t ca;
+        if (A.gamma[(size_t)Y * A.sy + X]) {
+            v = fine_at(A.g, A.sy, X, Y);
+        } else if (tile_inflow(A, xl, yl, X, Y, ca)) {
+            v = A.U[ca];
+            wv = A.W[ca];
+        }
+        if (!same_bits(v, su[f]) || wv != sw[f]) {
+            diff = true;
+            su[f] = v;
+            sw[f] = wv;
+        }
+    }
+    const bool solved = A.sig_ok[tile] != 0;
+    const bool need = __syncthreads_or(diff) || !solved;
+    if (need && threadIdx.x == 0) A.sig_ok[tile] = 1;
+    return need;
+}
+
 template <class T>
 __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int tile) {
     if (*A.done) return;
+    if (!tile_needs_solve(A, tile)) {
+        if (threadIdx.x == 0) atomicAdd(&A.st->fine_skips, 1ull);
+        return;
+    }
     const DDGeom &G = A.G;
     const T INF = Num<T>::inf();
     const int tx = tile % G.tx, ty = tile / G.tx;
@@ -860,6 +933,7 @@ __device__ void init_body(const DDArgs<T> &A) {
         A.bar[0] = A.bar[1] = 0;
     }
     for (int k = threadIdx.x; k < A.max_iter + 2; k += blockDim.x) A.deltas[k] = k == 0 ? INFINITY : 0.0;
+    for (int t = threadIdx.x; t < A.G.tx * A.G.ty; t += blockDim.x) A.sig_ok[t] = 0;
 }
 
 template <class T>
@@ -883,6 +957,7 @@ __device__ void finalize_body(const DDArgs<T> &A, eik_dd_stats *out, long long l
     out->fine_updates = (int64_t)A.st->fine_updates;
     out->coarse_updates = (int64_t)A.st->coarse_updates;
     out->launches = launches;
+    out->fine_solves_skipped = (int64_t)A.st->fine_skips;
 }
 
 template <class T>

@@ -45,6 +45,9 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
     double *deltas = cv.take<double>((size_t)max_iter + 2);
     int *chg = cv.take<int>(4);
     int *ldirty = cv.take<int>((size_t)G.ncx + G.ncy + 2);
+    T *sig_u = cv.take<T>(ntiles * tile_face_count(G));
+    uint8_t *sig_w = cv.take<uint8_t>(ntiles * tile_face_count(G));
+    int *sig_ok = cv.take<int>(ntiles);
     unsigned *bar = cv.take<unsigned>(4);
     DevStats *st = cv.take<DevStats>(1);
     T *Ch[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -75,6 +78,9 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
         A->deltas = deltas;
         A->chg = chg;
         A->ldirty = ldirty;
+        A->sig_u = sig_u;
+        A->sig_w = sig_w;
+        A->sig_ok = sig_ok;
         A->bar = bar;
         A->st = st;
     }
@@ -104,7 +110,7 @@ inline int causal_shape(const void *kernel, int lw, int lines, int nsm, int smem
         cs.smem = 0;
         cs.lw = 0;
     }
-    int rc = cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs.smem),
+    int rc = cuda_check(set_dyn_smem(kernel, (int)cs.smem),
                         "smem attr causal");
     if (rc) return rc;
     int per_sm = 0;

@@ -346,14 +346,12 @@ static int adj_run(const eik_grid *grid, const AdjPlan &P, const void *r, const 
     EIK_LAUNCH("adj_nodes", s, k_adj_nodes<T><<<tb, 256, 0, s>>>(A));
     EIK_LAUNCH("adj_pack", s, k_adj_pack<T><<<tb, 256, 0, s>>>(A));
     if (single) {
-        if ((rc = cuda_check(cudaFuncSetAttribute(k_adj_run<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P.smem), "smem attr")))
+        if ((rc = cuda_check(set_dyn_smem(k_adj_run<T>, (int)P.smem), "smem attr")))
             return rc;
         EIK_LAUNCH("adj_sweeps", s, k_adj_run<T><<<1, 32 * P.nb, P.smem, s>>>(A));
     } else {
         const int nblk = (P.nb + P.wpc - 1) / P.wpc;
-        if ((rc = cuda_check(cudaFuncSetAttribute(k_adj_run_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P.gsmem), "smem attr")))
+        if ((rc = cuda_check(set_dyn_smem(k_adj_run_global<T>, (int)P.gsmem), "smem attr")))
             return rc;
         int per_sm = 0;
         if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_run_global<T>, 32 * P.wpc,
@@ -526,8 +524,7 @@ static int adj_many_run(const eik_grid *grid, const AdjManyPlan &MP, int nprob, 
     const int nblk = (P.nb + P.wpc - 1) / P.wpc;
     int group = nprob;
     if (!single) {
-        if ((rc = cuda_check(cudaFuncSetAttribute(k_adjm_run_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P.gsmem), "smem attr")))
+        if ((rc = cuda_check(set_dyn_smem(k_adjm_run_global<T>, (int)P.gsmem), "smem attr")))
             return rc;
         int per_sm = 0;
         if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjm_run_global<T>, 32 * P.wpc,
@@ -539,8 +536,7 @@ static int adj_many_run(const eik_grid *grid, const AdjManyPlan &MP, int nprob, 
                       per_sm * nsm);
             return EIK_EUNSUPPORTED;
         }
-    } else if ((rc = cuda_check(cudaFuncSetAttribute(k_adjm_run<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)P.smem), "smem attr"))) {
+    } else if ((rc = cuda_check(set_dyn_smem(k_adjm_run<T>, (int)P.smem), "smem attr"))) {
         return rc;
     }
     std::vector<const void *> tab((size_t)4 * nprob);

@@ -83,9 +83,9 @@ int dd3_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const voi
             void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s);
 // 1-D implementation (eik_dd1.cu)
 bool dd1_validate(const eik_grid *grid, const eik_dd_params *p);
-size_t dd1_workspace_size();
+size_t dd1_workspace_size(const eik_grid *grid, const eik_dd_params *p);
 int dd1_run(const eik_grid *grid, const void *r, const uint8_t *gamma, const void *g, const eik_dd_params *p,
-            void *u_out, eik_dd_stats *stats, cudaStream_t s);
+            void *u_out, void *ws, eik_dd_stats *stats, cudaStream_t s);
 
 // Parameters of the per-node weight of Sec. 4.2 (2-D and 3-D).
 static bool valid_adaptive(const eik_dd_params *p) {
@@ -210,15 +210,12 @@ struct DDSolve {
                       P.step4_smem, smem_optin);
             return EIK_EUNSUPPORTED;
         }
-        if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::fine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)fine_smem), "smem attr fine")))
+        if ((rc = cuda_check(set_dyn_smem(DDKernels<T>::fine, (int)fine_smem), "smem attr fine")))
             return rc;
-        if ((rc = cuda_check(cudaFuncSetAttribute(DDKernels<T>::step1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P.step1_smem), "smem attr step1")))
+        if ((rc = cuda_check(set_dyn_smem(DDKernels<T>::step1, (int)P.step1_smem), "smem attr step1")))
             return rc;
         step4k = P.adaptive ? DDKernels<T>::step4a : DDKernels<T>::step4;
-        if ((rc = cuda_check(cudaFuncSetAttribute(step4k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P.step4_smem), "smem attr step4")))
+        if ((rc = cuda_check(set_dyn_smem(step4k, (int)P.step4_smem), "smem attr step4")))
             return rc;
         // causal sweep: cooperative grid sized to what is co-resident
         if ((rc = causal_shape<T>((const void *)k_causal<T>, std::max(G.nx, G.ny), std::max(G.ncx, G.ncy) + 1, nsm,
@@ -313,7 +310,7 @@ using namespace eik;
 
 extern "C" size_t eik_dd_workspace_size(const eik_grid *grid, const eik_dd_params *params) {
     if (!dd_validate(grid, params)) return 0;
-    if (grid->ndim == 1) return dd1_workspace_size();
+    if (grid->ndim == 1) return dd1_workspace_size(grid, params);
     if (grid->ndim == 3) return dd3_workspace_size(grid, params);
     return dd_plan(grid, params).bytes;
 }
@@ -330,7 +327,7 @@ extern "C" int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *
         set_error("workspace must be 256-byte aligned");
         return EIK_EINVAL;
     }
-    const size_t need = grid->ndim == 1   ? dd1_workspace_size()
+    const size_t need = grid->ndim == 1   ? dd1_workspace_size(grid, params)
                         : grid->ndim == 3 ? dd3_workspace_size(grid, params)
                                           : dd_plan(grid, params).bytes;
     if (ws_bytes < need) {
@@ -338,7 +335,7 @@ extern "C" int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *
         return EIK_ENOMEM;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (grid->ndim == 1) return dd1_run(grid, r, gamma, g, params, u_out, stats, s);
+    if (grid->ndim == 1) return dd1_run(grid, r, gamma, g, params, u_out, ws, stats, s);
     if (grid->ndim == 3) return dd3_run(grid, r, gamma, g, params, u_out, ws, stats, s);
     if (grid->dtype == EIK_F64) return dd_run<double>(grid, r, gamma, g, params, u_out, ws, stats, s);
     return dd_run<float>(grid, r, gamma, g, params, u_out, ws, stats, s);

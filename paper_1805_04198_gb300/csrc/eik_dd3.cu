@@ -753,6 +753,7 @@ __global__ void k3_finalize(DD3Args<T> A, eik_dd_stats *out, long long launches)
     out->fine_updates = (int64_t)A.st->fine_updates;
     out->coarse_updates = (int64_t)A.st->coarse_updates;
     out->launches = launches;
+    out->fine_solves_skipped = 0;
 }
 
 // --------------------------------------------------------------------------
@@ -936,11 +937,11 @@ static int dd3_run_t(const eik_grid *grid, const void *r, const uint8_t *gamma, 
                   P.grid_smem, optin);
         return EIK_EUNSUPPORTED;
     }
-    if ((rc = cuda_check(cudaFuncSetAttribute(k3_fine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.fine_smem), "attr")))
+    if ((rc = cuda_check(set_dyn_smem(k3_fine<T>, (int)P.fine_smem), "attr")))
         return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(k3_step1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grid_smem), "attr")))
+    if ((rc = cuda_check(set_dyn_smem(k3_step1<T>, (int)P.grid_smem), "attr")))
         return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(k3_step4<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.grid_smem), "attr")))
+    if ((rc = cuda_check(set_dyn_smem(k3_step4<T>, (int)P.grid_smem), "attr")))
         return rc;
     const int causal_threads = 256;
     int per_sm = 0;

@@ -503,14 +503,11 @@ static int batch_run(int nprob, const eik_grid *grids, const void *const *r, con
         set_error("shared memory need (%zu, %zu) exceeds the device limit %d", need_fine, need_grid, smem_optin);
         return EIK_EUNSUPPORTED;
     }
-    if ((rc = cuda_check(cudaFuncSetAttribute(BatchKernels<T>::fine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)std::max<size_t>(need_fine, 1)), "smem attr fine")))
+    if ((rc = cuda_check(set_dyn_smem(BatchKernels<T>::fine, (int)std::max<size_t>(need_fine, 1)), "smem attr fine")))
         return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(BatchKernels<T>::step1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)std::max<size_t>(need_grid, 1)), "smem attr step1")))
+    if ((rc = cuda_check(set_dyn_smem(BatchKernels<T>::step1, (int)std::max<size_t>(need_grid, 1)), "smem attr step1")))
         return rc;
-    if ((rc = cuda_check(cudaFuncSetAttribute(step4k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)std::max<size_t>(need_grid, 1)), "smem attr step4")))
+    if ((rc = cuda_check(set_dyn_smem(step4k, (int)std::max<size_t>(need_grid, 1)), "smem attr step4")))
         return rc;
 
     // launch shapes of the box classes

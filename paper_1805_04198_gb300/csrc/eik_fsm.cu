@@ -290,15 +290,13 @@ static int fsm_run(const eik_grid *grid, const FsmPlan &P, const void *r, const 
     const int tb = (int)std::min<size_t>((total + 255) / 256, (size_t)nsm * 16);
     EIK_LAUNCH("fsm_pack", s, k_fsm_pack<T><<<tb, 256, 0, s>>>(A));
     if (single) {
-        if ((rc = cuda_check(cudaFuncSetAttribute(k_fsm_run<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P.smem), "smem attr")))
+        if ((rc = cuda_check(set_dyn_smem(k_fsm_run<T>, (int)P.smem), "smem attr")))
             return rc;
         EIK_LAUNCH("fsm_sweeps", s, k_fsm_run<T><<<1, 32 * P.nb, P.smem, s>>>(A));
     } else {
         // one CTA per P.wpc blocks, all co-resident
         const int nblk = (P.nb + P.wpc - 1) / P.wpc;
-        if ((rc = cuda_check(cudaFuncSetAttribute(k_fsm_run_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P.gsmem), "smem attr")))
+        if ((rc = cuda_check(set_dyn_smem(k_fsm_run_global<T>, (int)P.gsmem), "smem attr")))
             return rc;
         int per_sm = 0;
         if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsm_run_global<T>, 32 * P.wpc,
@@ -439,8 +437,7 @@ static int fsm_many_run(const eik_grid *grid, const FsmManyPlan &MP, int nprob, 
     const int nblk = (P.nb + P.wpc - 1) / P.wpc;
     int group = nprob;  // problems per cooperative launch
     if (!single) {
-        if ((rc = cuda_check(cudaFuncSetAttribute(k_fsmm_run_global<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P.gsmem), "smem attr")))
+        if ((rc = cuda_check(set_dyn_smem(k_fsmm_run_global<T>, (int)P.gsmem), "smem attr")))
             return rc;
         int per_sm = 0;
         if ((rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsmm_run_global<T>, 32 * P.wpc,
@@ -452,8 +449,7 @@ static int fsm_many_run(const eik_grid *grid, const FsmManyPlan &MP, int nprob, 
                       per_sm * nsm);
             return EIK_EUNSUPPORTED;
         }
-    } else if ((rc = cuda_check(cudaFuncSetAttribute(k_fsmm_run<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)P.smem), "smem attr"))) {
+    } else if ((rc = cuda_check(set_dyn_smem(k_fsmm_run<T>, (int)P.smem), "smem attr"))) {
         return rc;
     }
     // pointer table: gamma, g, u
@@ -504,6 +500,7 @@ int set_spin_limit_batch(long long);
 int set_spin_limit_dd3(long long);
 int set_spin_limit_fsm3(long long);
 int set_spin_limit_adj(long long);
+int set_spin_limit_dd1(long long);
 }  // namespace eik
 
 extern "C" int eik_set_wait_limit(int64_t iterations) {
@@ -513,7 +510,8 @@ extern "C" int eik_set_wait_limit(int64_t iterations) {
     }
     const long long v = iterations == 0 ? SPIN_LIMIT_DEFAULT : (long long)iterations;
     int (*const setters[])(long long) = {set_spin_limit_fsm, set_spin_limit_dd, set_spin_limit_batch,
-                                         set_spin_limit_dd3, set_spin_limit_fsm3, set_spin_limit_adj};
+                                         set_spin_limit_dd3, set_spin_limit_fsm3, set_spin_limit_adj,
+                                         set_spin_limit_dd1};
     for (auto f : setters) {
         const int rc = cuda_check((cudaError_t)f(v), "cudaMemcpyToSymbol(wait limit)");
         if (rc) return rc;

@@ -29,6 +29,18 @@ struct Carver {
     }
 };
 
+// Dynamic shared memory of a kernel, and the preference for the largest
+// shared-memory carveout: without it the runtime may pick a carveout that
+// holds one CTA of a kernel whose CTAs need just under half an SM's shared
+// memory, halving its occupancy.
+template <class F>
+inline cudaError_t set_dyn_smem(F *func, int bytes) {
+    cudaError_t e = cudaFuncSetAttribute((const void *)func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
 inline int cuda_check(cudaError_t e, const char *what) {
     if (e != cudaSuccess) {
         set_error("%s: %s", what, cudaGetErrorString(e));

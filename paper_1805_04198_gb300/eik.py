@@ -60,7 +60,8 @@ class DDStats(ctypes.Structure):
                 ("causal_rounds_max", ctypes.c_int), ("fsm_sweeps_max", ctypes.c_int64),
                 ("coarse_sweeps_max", ctypes.c_int64), ("fsm_cap_hits", ctypes.c_int64),
                 ("coarse_cap_hits", ctypes.c_int64), ("last_delta", ctypes.c_double),
-                ("fine_updates", ctypes.c_int64), ("coarse_updates", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("fine_updates", ctypes.c_int64), ("coarse_updates", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("fine_solves_skipped", ctypes.c_int64)]
 
 
 class AdjointStats(ctypes.Structure):

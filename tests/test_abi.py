@@ -81,11 +81,12 @@ def test_noalloc_scratch_size_matches_header(lib):
 
 
 def test_one_dimensional_requests(lib):
-    """1-D grids go to the Sec. 3.1 solve: a valid request needs 256 bytes
-    (no workspace); coarse_ratio must be the subinterval width, at most 2048
-    subintervals, no per-node weight; the other entry points reject 1-D."""
+    """1-D grids go to the Sec. 3.1 solve: a valid request needs a few kB
+    (control words, U, W and the end copies); coarse_ratio must be the
+    subinterval width, at most 2048 subintervals, no per-node weight; the
+    other entry points reject 1-D."""
     g = lib.Grid(1, 1, (ctypes.c_int64 * 3)(1001, 1, 1), (ctypes.c_int64 * 3)(1, 1001, 1001), 1e-3)
-    assert lib.eik_dd_workspace_size(g, lib.dd_params((10,), 100)) == 256
+    assert 0 < lib.eik_dd_workspace_size(g, lib.dd_params((10,), 100)) <= 4096
     assert lib.eik_dd_workspace_size(g, lib.dd_params((10,), 50)) == 0
     assert "coarse_ratio" in lib.eik_last_error()
     assert lib.eik_dd_workspace_size(g, lib.dd_params((7,), 100)) == 0
@@ -94,7 +95,7 @@ def test_one_dimensional_requests(lib):
     assert lib.eik_dd_workspace_size(big, lib.dd_params((2049,), 2)) == 0
     assert "2048" in lib.eik_last_error()
     ok = lib.Grid(1, 0, (ctypes.c_int64 * 3)(2048 * 2 + 1, 1, 1), (ctypes.c_int64 * 3)(1, 1, 1), 1e-3)
-    assert lib.eik_dd_workspace_size(ok, lib.dd_params((2048,), 2)) == 256
+    assert 0 < lib.eik_dd_workspace_size(ok, lib.dd_params((2048,), 2)) <= 64 * 1024
     assert lib.eik_fsm_workspace_size(g) == 0
     with pytest.raises(lib.EikError, match="2-D"):
         lib.eik_dd_shard_exchange_bytes(g, lib.dd_params((10,), 100))

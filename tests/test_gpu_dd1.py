@@ -80,7 +80,7 @@ def test_fp64_bitwise_against_oracle(name):
         assert st[k] == st_o[k], (k, st[k], st_o[k])
     if st_o["iters"] >= 1:
         assert st["last_delta"] == st_o["last_delta"]
-    assert st["launches"] == 1
+    assert st["launches"] == 1 and st["error"] == 0
 
 
 @pytest.mark.parametrize("name", ["bump_M100_theta1", "inner_sources_no_convergence", "2048_subintervals", "long_subintervals"])
@@ -125,3 +125,26 @@ def test_noalloc_entry_point_equals_dd_solve():
     eik.eik_dd_solve_noalloc(eik.make_grid(R, h), R, G, Gv, eik.dd_params((37,), 27, **kw), u2, sd)
     torch.cuda.synchronize()
     assert torch.equal(u, u2) and eik.parse_dd_stats(sd) == st
+
+
+def test_expired_barrier_reports_timeout_then_solves_exactly():
+    """The grid barriers between the fine and coarse phases are bounded waits:
+    with a one-poll limit some expires, the call ends with
+    EIK_EDEVICE_TIMEOUT in its statistics, and with the default limit back
+    the same context gives the oracle's result bitwise."""
+    make, N, M, kw = CASES["2048_subintervals"]
+    r, gam, g, h = make()
+    kw = dict(kw, max_coarse_sweeps=1000)
+    eik.eik_set_wait_limit(1)
+    try:
+        R = torch.from_numpy(r).to(DEV)
+        u, sd = eik.dd_solve(R, torch.from_numpy(gam).to(DEV), torch.from_numpy(g).to(DEV), h, (N,), M,
+                             sync=False, **kw)
+        torch.cuda.synchronize()
+        assert eik.parse_dd_stats(sd)["error"] == -4
+    finally:
+        eik.eik_set_wait_limit(0)
+    u_o, st_o, _ = O.dd1(r, gam, g, h, N, M, **kw)
+    u, st = _gpu(r, gam, g, h, N, M, torch.float64, **kw)
+    assert st["error"] == 0
+    np.testing.assert_array_equal(u.cpu().numpy(), u_o)

@@ -30,7 +30,8 @@ def _two_slab_solve(r, gamma, g, h, tiles, c, world=2, **params):
                 if dst is not src:
                     dst.xbuf[a * tx * rec: b * tx * rec] = src.xbuf[a * tx * rec: b * tx * rec]
         sts = [p.coarse(k) for p in procs]
-        local = ("launches", "fine_updates", "fsm_sweeps_max", "fsm_cap_hits")  # per process: its subdomains
+        local = ("launches", "fine_updates", "fsm_sweeps_max", "fsm_cap_hits",  # per process: its subdomains
+                 "fine_solves_skipped")
         for st in sts[1:]:
             assert {kk: v for kk, v in st.items() if kk not in local} == \
                    {kk: v for kk, v in sts[0].items() if kk not in local}
@@ -52,6 +53,7 @@ def _two_slab_solve(r, gamma, g, h, tiles, c, world=2, **params):
     st = dict(sts[0])
     st["fine_updates"] = sum(x["fine_updates"] for x in sts)
     st["fsm_cap_hits"] = sum(x["fsm_cap_hits"] for x in sts)
+    st["fine_solves_skipped"] = sum(x["fine_solves_skipped"] for x in sts)
     st["fsm_sweeps_max"] = max(x["fsm_sweeps_max"] for x in sts)
     return u, st
 
@@ -71,7 +73,8 @@ def test_two_slabs_equal_single_solve_bitwise(shape, tiles, c, dtype, theta, kma
     kw = dict(theta=theta, max_iter=kmax, tol=tol, max_coarse_sweeps=8)
     ref, st_ref = eik.dd_solve(R, G, g_t, h, tiles, c, **kw)
     u, st = _two_slab_solve(R, G, g_t, h, tiles, c, **kw)
-    for key in ("iters", "converged", "error", "fine_updates", "coarse_updates", "fsm_sweeps_max"):
+    for key in ("iters", "converged", "error", "fine_updates", "coarse_updates", "fsm_sweeps_max",
+                "fine_solves_skipped"):
         assert st[key] == st_ref[key], key
     np.testing.assert_array_equal(u.cpu().numpy(), ref.cpu().numpy())
 
