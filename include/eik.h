@@ -190,6 +190,22 @@ int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *gamma, cons
                  eik_dd_stats *stats, void *stream);
 
 /*
+ * eik_dd_coarse_state: the coarse state a 2-D DD workspace holds (same grid
+ * and params as the call that filled it, after `stream` has run that call),
+ * scattered to fine indexing: U at every coarse-set node into U_out (grid
+ * dtype, strides of grid) and W into W_out (one byte per node: wind
+ * components w_a = ((byte >> 2a) & 3) - 1, a = x, y).  After
+ * eik_dd_shard_start (set-up, Step 1, causal sweep) that is U^0, W^0.  After
+ * eik_dd_solve or eik_dd_shard_coarse stopped at iteration k it is U^k (u^k
+ * with the constant weight 0, whose Step 4 result Alg. 4 writes in place) and
+ * W = w^k (Alg. 4 sets W to the chosen fine winds).  Other nodes are left
+ * untouched; either output may be NULL.  Returns EIK_OK, EIK_EINVAL,
+ * EIK_ENOMEM, EIK_ECUDA or EIK_EUNSUPPORTED (3-D and 1-D).
+ */
+int eik_dd_coarse_state(const eik_grid *grid, const eik_dd_params *params, const void *ws, size_t ws_bytes,
+                        void *U_out, uint8_t *W_out, void *stream);
+
+/*
  * Sharded 2-D solve: the phases of eik_dd_solve for a caller that splits the
  * subdomain solves (Steps 2-3 of Sec. 3.2, which the paper runs "in parallel"
  * for every subdomain) over several processes, each owning a slab of

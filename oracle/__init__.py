@@ -20,6 +20,8 @@ Functions (each follows the paper section named in its docstring):
   theta_node   Sec. 4.2's weight of one node from its history
   dd_probe     dd with a per-iteration record of one node
   dd1          the one-dimensional method of Sec. 3.1 (Steps 1-4)
+  dd_margins   dd() plus W^0 and the margins of Step 1's wind decisions (for
+               tests of a lower-precision solve)
 """
 from __future__ import annotations
 
@@ -139,6 +141,9 @@ def _bind(lib):
     lib.orc_dd_probe.restype = ctypes.c_int
     lib.orc_dd_probe.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, dp, dp, ctypes.POINTER(DDStats),
                                  ctypes.c_long, dp]
+    lib.orc_dd_margins.restype = ctypes.c_int
+    lib.orc_dd_margins.argtypes = [ctypes.POINTER(DDParams), dp, bp, dp, dp, ctypes.POINTER(DDStats), sp, dp, dp, sp,
+                                   dp, dp]
     lib.orc_dd1.restype = ctypes.c_int
     lib.orc_dd1.argtypes = [ctypes.POINTER(DD1Params), dp, bp, dp, dp, dp, dp, dp, sp,
                             ctypes.POINTER(DD1Stats)]
@@ -243,6 +248,39 @@ def dd(r, gamma, g, h, tiles, c, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps
     if return_coarse:
         out = out + (U,)
     return out
+
+
+def dd_margins(r, gamma, g, h, tiles, c, theta=1.0, max_iter=0, tol=0.0, max_fsm_sweeps=100000,
+               max_coarse_sweeps=80, U0=None, W0=None, parallel=False):
+    """dd() with test hooks for comparing a lower-precision solve.  Returns
+    (u, stats, W0_own, margin, copies, cmargin): W0_own (shape + (3,)) is this
+    solve's W^0, margin (shape) at each coarse-set node the smallest margin of
+    the Alg. 1 decisions behind its wind (NaN off the coarse set, +inf at Gamma
+    and unreached nodes); copies (4 + shape) the subdomain copies of iteration
+    0 at the coarse-set nodes by slot (NaN where absent) and cmargin (shape) the
+    smallest margin of the decisions behind Alg. 4's choice there.  U0 (shape)
+    and W0 (shape + (3,)), when given, replace this solve's U^0 and W^0 at the
+    coarse-set nodes after Step 1."""
+    lib = _load(omp=parallel)
+    r, gamma, g = _prep(r, gamma, g)
+    p = _params(r.shape, h, tiles, c, theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps, False,
+                (1.0, 1.0, 1.0), 0.75, 0.01, 0.9, 0.0)
+    u = np.empty_like(r)
+    W0_own = np.zeros(r.shape + (3,), dtype=np.int8)
+    margin = np.empty_like(r)
+    copies = np.empty((4,) + r.shape)
+    cmargin = np.empty_like(r)
+    U0_in = None if U0 is None else np.ascontiguousarray(U0, dtype=np.float64)
+    W0_in = None if W0 is None else np.ascontiguousarray(W0, dtype=np.int8)
+    null_d = ctypes.POINTER(ctypes.c_double)()
+    null_s = ctypes.POINTER(ctypes.c_byte)()
+    st = DDStats()
+    rc = lib.orc_dd_margins(ctypes.byref(p), _dp(r), _bp(gamma), _dp(g), _dp(u), ctypes.byref(st), _sp(W0_own),
+                            _dp(margin), null_d if U0_in is None else _dp(U0_in),
+                            null_s if W0_in is None else _sp(W0_in), _dp(copies), _dp(cmargin))
+    if rc != 0:
+        raise ValueError("oracle dd_margins: invalid parameters")
+    return u, st.as_dict(), W0_own, margin, copies, cmargin
 
 
 def _params(shape, h, tiles, c, theta, max_iter, tol, max_fsm_sweeps, max_coarse_sweeps, theta_adaptive, omega,

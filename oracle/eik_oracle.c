@@ -488,6 +488,51 @@ static long step1_grid(const geom_t *G, const long *o, double H, const double *r
     return s;
 }
 
+/* Decision margins of Alg. 1 at the nodes of one shifted grid, at its
+ * converged Step 1 values (test infrastructure, no part of the method): per
+ * node the smallest of |vm - vp| on each axis (which neighbour an axis takes),
+ * | |a0 - a1| - rH | (two-axis or one-axis branch) and |a0 - a1| (the axis of
+ * the one-axis branch), over the pairs of the 2-D local solve; +inf where a
+ * compared pair holds an infinite value.  A wind whose margin is below the
+ * error of a lower-precision evaluation of U may come out otherwise there. */
+static void step1_margins(const geom_t *G, const long *o, double H, const double *r, const unsigned char *gamma,
+                          const double *U, double *margin)
+{
+    long m[3], M, x, y, z;
+    double *ul;
+    grid_box(G, o, m);
+    M = m[0] * m[1] * m[2];
+    ul = malloc(sizeof(double) * (size_t)M);
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) ul[lidx(m, x, y, z)] = U[grid_fine(G, o, x, y, z)];
+    for (z = 0; z < m[2]; ++z)
+        for (y = 0; y < m[1]; ++y)
+            for (x = 0; x < m[0]; ++x) {
+                long f = grid_fine(G, o, x, y, z), l = lidx(m, x, y, z);
+                double vm[3], vp[3], a[3], mg = INF, rH = r[f] * H;
+                int k, j;
+                if (gamma[f] || !(ul[l] < INF)) {
+                    margin[f] = INF;
+                    continue;
+                }
+                nbrs(G->d, m, ul, x, y, z, vm, vp);
+                for (k = 0; k < G->d; ++k) {
+                    double dv = fabs(vm[k] - vp[k]);
+                    if (dv < mg) mg = dv;
+                    a[k] = vm[k] < vp[k] ? vm[k] : vp[k];
+                }
+                for (k = 0; k < G->d; ++k)
+                    for (j = k + 1; j < G->d; ++j) {
+                        double t = fabs(a[k] - a[j]);
+                        if (t < mg) mg = t;
+                        if (fabs(t - rH) < mg) mg = fabs(t - rH);
+                    }
+                margin[f] = mg;
+            }
+    free(ul);
+}
+
 /* Per-node weight of Sec. 4.2.  The bound M-bar of Theorem 2 is estimated by
  * eq. secthetaest: the last change of the fine values over a weighted mean of
  * the last changes of the coarse solver,
@@ -923,9 +968,93 @@ static double coarse_delta(const geom_t *G, const double *U1, const double *U0)
     return dmax;
 }
 
+/* Test hooks of dd_iterate (all optional): Step 1's W^0 and decision
+ * margins out; U^0, W^0 replaced by given ones after Step 1; the subdomain
+ * copies of iteration 0 at the coarse-set nodes and the margins of the
+ * decisions behind Alg. 4's choice among them out. */
+typedef struct {
+    signed char *W0_out;
+    double *margin_out;
+    const double *U0_in;
+    const signed char *W0_in;
+    double *copies_out;  /* [4][N], slot as in the copy export below, NaN where absent */
+    double *cmargin_out; /* [N] */
+} dd_hooks;
+
+/* Alg. 3 decision margin at node l of a subdomain's final state (spacing h,
+ * one-sided at the box edges), as step1_margins; for an inflow node also the
+ * gap between its starting value and the local solve (whether it kept U, the
+ * echo rule of the copies). */
+static double tile_node_margin(int d, const long *m, double rh, const double *ut, long x, long y, long z,
+                               int inflow, double u0)
+{
+    double vm[3], vp[3], a[3], mg = INF;
+    signed char w[3];
+    int k, j;
+    nbrs(d, m, ut, x, y, z, vm, vp);
+    for (k = 0; k < d; ++k) {
+        double dv = fabs(vm[k] - vp[k]);
+        if (dv < mg) mg = dv;
+        a[k] = vm[k] < vp[k] ? vm[k] : vp[k];
+    }
+    for (k = 0; k < d; ++k)
+        for (j = k + 1; j < d; ++j) {
+            double t = fabs(a[k] - a[j]);
+            if (t < mg) mg = t;
+            if (fabs(t - rh) < mg) mg = fabs(t - rh);
+        }
+    if (inflow) {
+        double ls = orc_local_solve(d, vm, vp, rh, w);
+        if (fabs(ls - u0) < mg) mg = fabs(ls - u0);
+    }
+    return mg;
+}
+
+/* The copies of every subdomain at its coarse-set nodes (slot bit 0: the node
+ * is the subdomain's x = 0 face on an interior x interface, bit 1 the same for
+ * y), and per node the smallest decision margin over its copies.  (Copies
+ * closer than the compared precision's error may be chosen either way without
+ * moving the result beyond it, so their gap is no decision margin.) */
+static void export_copies(const geom_t *G, double h, const double *r, const unsigned char *gamma, const double *U,
+                          const signed char *W, double **tu, double *copies, double *cmargin)
+{
+    long ti, ntiles = (long)G->T[0] * G->T[1] * G->T[2], i, m[3];
+    int k;
+    for (k = 0; k < 3; ++k) m[k] = (k < G->d) ? G->S[k] + 1 : 1;
+    for (i = 0; i < 4 * G->N; ++i) copies[i] = NAN;
+    for (i = 0; i < G->N; ++i) cmargin[i] = NAN;
+    for (ti = 0; ti < ntiles; ++ti) {
+        int t[3];
+        long x, y, z;
+        t[0] = (int)(ti % G->T[0]);
+        t[1] = (int)((ti / G->T[0]) % G->T[1]);
+        t[2] = (int)(ti / ((long)G->T[0] * G->T[1]));
+        for (z = 0; z < m[2]; ++z)
+            for (y = 0; y < m[1]; ++y)
+                for (x = 0; x < m[0]; ++x) {
+                    long lc[3] = {x, y, z}, xf[3], f, l = lidx(m, x, y, z);
+                    int slot = 0, inflow = 0;
+                    double mg;
+                    for (k = 0; k < 3; ++k) xf[k] = (k < G->d) ? t[k] * G->S[k] + lc[k] : 0;
+                    if (!coarse_axes(G, xf)) continue;
+                    f = xf[0] + G->n[0] * (xf[1] + G->n[1] * xf[2]);
+                    if (G->d >= 1 && lc[0] == 0 && xf[0] > 0 && xf[0] < G->n[0] - 1) slot |= 1;
+                    if (G->d >= 2 && lc[1] == 0 && xf[1] > 0 && xf[1] < G->n[1] - 1) slot |= 2;
+                    copies[(long)slot * G->N + f] = tu[ti][l];
+                    if (gamma[f] || !(tu[ti][l] < INF)) continue;
+                    for (k = 0; k < G->d; ++k) {
+                        if (lc[k] == 0 && W[3 * f + k] > 0) inflow = 1;
+                        if (lc[k] == m[k] - 1 && W[3 * f + k] < 0) inflow = 1;
+                    }
+                    mg = tile_node_margin(G->d, m, r[f] * h, tu[ti], x, y, z, inflow, U[f]);
+                    if (isnan(cmargin[f]) || mg < cmargin[f]) cmargin[f] = mg;
+                }
+    }
+}
+
 static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
                       double *u_out, double *U_out, double *delta_log, orc_dd_stats *st, long probe,
-                      double *probe_log)
+                      double *probe_log, const dd_hooks *hk)
 {
     geom_t G;
     long i, ntiles;
@@ -1029,10 +1158,20 @@ static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned ch
             S0.coarse_updates += (long long)gsweeps[q] * m[0] * m[1] * m[2];
         }
     }
+    if (hk && hk->margin_out) {
+        long q;
+        for (i = 0; i < G.N; ++i) hk->margin_out[i] = NAN;
+        for (q = 0; q < ngrid; ++q) step1_margins(&G, offs + 3 * q, H, r, gamma, U, hk->margin_out);
+    }
     {
         long cr = causal_sweep(&G, U, W);
         if (cr > S0.causal_rounds_max) S0.causal_rounds_max = cr;
     }
+    if (hk && hk->W0_out) memcpy(hk->W0_out, W, (size_t)(3 * G.N));
+    if (hk && hk->U0_in)
+        for (i = 0; i < G.N; ++i)
+            if (!isnan(U[i])) U[i] = hk->U0_in[i];
+    if (hk && hk->W0_in) memcpy(W, hk->W0_in, (size_t)(3 * G.N));
     if (delta_log)
         for (k = 0; k <= p->max_iter; ++k) delta_log[k] = NAN;
     if (delta_log) delta_log[0] = INF;
@@ -1058,6 +1197,7 @@ static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned ch
         }
         /* Alg. 4 */
         alg4(&G, tu, tw, te, W, uk, wk);
+        if (hk && hk->copies_out && it == 0) export_copies(&G, p->h, r, gamma, U, W, tu, hk->copies_out, hk->cmargin_out);
         if (thfull) {
             probe_log[4 * it + 0] = uk[probe];
             probe_log[4 * it + 3] = U[probe];
@@ -1166,14 +1306,28 @@ static int dd_iterate(const orc_dd_params *p, const double *r, const unsigned ch
 int orc_dd(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
            double *u_out, double *U_out, double *delta_log, orc_dd_stats *st)
 {
-    return dd_iterate(p, r, gamma, g, u_out, U_out, delta_log, st, -1, NULL);
+    return dd_iterate(p, r, gamma, g, u_out, U_out, delta_log, st, -1, NULL, NULL);
 }
 
 int orc_dd_probe(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
                  double *u_out, double *U_out, double *delta_log, orc_dd_stats *st, long probe_node,
                  double *probe_log)
 {
-    return dd_iterate(p, r, gamma, g, u_out, U_out, delta_log, st, probe_node, probe_log);
+    return dd_iterate(p, r, gamma, g, u_out, U_out, delta_log, st, probe_node, probe_log, NULL);
+}
+
+int orc_dd_margins(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
+                   double *u_out, orc_dd_stats *st, signed char *W0_out, double *margin_out,
+                   const double *U0_in, const signed char *W0_in, double *copies_out, double *cmargin_out)
+{
+    dd_hooks hk;
+    hk.W0_out = W0_out;
+    hk.margin_out = margin_out;
+    hk.U0_in = U0_in;
+    hk.W0_in = W0_in;
+    hk.copies_out = (copies_out && cmargin_out) ? copies_out : NULL;
+    hk.cmargin_out = cmargin_out;
+    return dd_iterate(p, r, gamma, g, u_out, NULL, NULL, st, -1, NULL, &hk);
 }
 
 /* ------------------------------------------------------------------------- */

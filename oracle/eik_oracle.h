@@ -122,6 +122,23 @@ int orc_dd_probe(const orc_dd_params *p, const double *r, const unsigned char *g
                  double *u_out, double *U_out, double *delta_log, orc_dd_stats *st, long probe_node,
                  double *probe_log);
 
+/* orc_dd with hooks for tests that compare a lower-precision solve (every
+ * pointer may be NULL).  W0_out [3 N] = W^0 (three components per node; 0 off
+ * the coarse set) and margin_out [N] = at each coarse-set node the smallest
+ * margin of the Alg. 1 decisions behind its wind (NaN elsewhere), both from
+ * this solve's own Step 1.  U0_in [N] / W0_in [3 N] replace U^0 / W^0 at the
+ * coarse-set nodes after Step 1 (the other solve's Step 1), so that Steps 2-3
+ * and Alg. 4 take that solve's Step 2 decisions.  copies_out [4 N] = the
+ * subdomain copies of iteration 0 at the coarse-set nodes (slot bit 0: the
+ * node lies on the subdomain's x = 0 face on an interior x interface, bit 1 the
+ * same for y; NaN where absent) and cmargin_out [N] = per coarse-set node the
+ * smallest margin of the decisions behind Alg. 4's choice (Alg. 3 at each
+ * copy, whether an inflow copy kept U).  Test
+ * infrastructure: the method's arithmetic is orc_dd's. */
+int orc_dd_margins(const orc_dd_params *p, const double *r, const unsigned char *gamma, const double *g,
+                   double *u_out, orc_dd_stats *st, signed char *W0_out, double *margin_out,
+                   const double *U0_in, const signed char *W0_in, double *copies_out, double *cmargin_out);
+
 /* The one-dimensional method of Sec. 3.1.  Fine grid of N*M+1 nodes, spacing
  * h; coarse nodes every M fine nodes (H = M h). */
 typedef struct {

@@ -342,6 +342,63 @@ extern "C" int eik_dd_solve(const eik_grid *grid, const void *r, const uint8_t *
 }
 
 // --------------------------------------------------------------------------
+// Read-back of the coarse state (U, W) of the last iteration of a 2-D solve,
+// scattered from the workspace's coarse layout to fine indexing.
+// --------------------------------------------------------------------------
+namespace eik {
+
+template <class T>
+__global__ void k_coarse_state(DDGeom G, const T *U, const uint8_t *W, T *U_out, uint8_t *W_out, long long sy) {
+    const long long n = (long long)G.nx * G.ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(e % G.nx), Y = (int)(e / G.nx);
+        if (!in_coarse_set(G, X, Y)) continue;
+        const size_t ca = coarse_addr(G, X, Y);
+        if (U_out) U_out[(size_t)Y * sy + X] = U[ca];
+        if (W_out) W_out[(size_t)Y * sy + X] = (uint8_t)(W[ca] & ~WIND_ECHO);
+    }
+}
+
+template <class T>
+static int coarse_state_t(const eik_grid *grid, const eik_dd_params *p, const void *ws, void *U_out, uint8_t *W_out,
+                          cudaStream_t s) {
+    const DDPlan P = dd_plan(grid, p);
+    DDArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    dd_layout<T>(P, &A, const_cast<void *>(ws), p->max_iter);
+    int dev, nsm = 0;
+    int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    EIK_LAUNCH("dd_coarse_state", s,
+               k_coarse_state<T><<<4 * nsm, 256, 0, s>>>(P.G, A.U, A.W, static_cast<T *>(U_out), W_out,
+                                                          grid->stride[1]));
+    return cuda_check(cudaGetLastError(), "coarse state launch");
+}
+
+}  // namespace eik
+
+extern "C" int eik_dd_coarse_state(const eik_grid *grid, const eik_dd_params *params, const void *ws,
+                                   size_t ws_bytes, void *U_out, uint8_t *W_out, void *stream) {
+    if (!dd_validate(grid, params)) return EIK_EINVAL;
+    if (grid->ndim != 2) {
+        set_error("eik_dd_coarse_state: 2-D solves only");
+        return EIK_EUNSUPPORTED;
+    }
+    if (!ws || (!U_out && !W_out) || (reinterpret_cast<uintptr_t>(ws) & 255)) {
+        set_error("eik_dd_coarse_state: NULL or unaligned argument");
+        return EIK_EINVAL;
+    }
+    if (ws_bytes < dd_plan(grid, params).bytes) {
+        set_error("workspace of %zu bytes is smaller than the solve's", ws_bytes);
+        return EIK_ENOMEM;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grid->dtype == EIK_F64) return coarse_state_t<double>(grid, params, ws, U_out, W_out, s);
+    return coarse_state_t<float>(grid, params, ws, U_out, W_out, s);
+}
+
+// --------------------------------------------------------------------------
 // Sharded 2-D solve: phases of eik_dd_solve for callers that split the
 // subdomain solves over several processes (slabs of subdomain rows) and keep
 // the coarse state replicated.

@@ -109,6 +109,9 @@ def load():
         lib.eik_dd_adjoint.restype = ctypes.c_int
         lib.eik_dd_adjoint.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, vp, vp, ctypes.c_int64, vp, ctypes.c_size_t,
                                        vp, vp]
+        lib.eik_dd_coarse_state.restype = ctypes.c_int
+        lib.eik_dd_coarse_state.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(DDParams), vp, ctypes.c_size_t, vp,
+                                            vp, vp]
         lib.eik_dd_solve_noalloc.restype = ctypes.c_int
         lib.eik_dd_solve_noalloc.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.POINTER(DDParams), vp, vp, vp]
         pp = ctypes.POINTER(ctypes.c_void_p)
@@ -283,6 +286,30 @@ def eik_dd_solve(grid, r, gamma, g, params, u_out, ws, stats_dev, stream=None):
                             wsp, wsn, _ptr(stats_dev), _stream(stream)))
 
 
+def eik_dd_coarse_state(grid, params, ws, U_out, W_out, stream=None):
+    lib = load()
+    wsp, wsn = _aligned(ws)
+    _check(lib.eik_dd_coarse_state(ctypes.byref(grid), ctypes.byref(params), wsp, wsn, _ptr(U_out), _ptr(W_out),
+                                   _stream(stream)))
+
+
+def dd_step1_state(r, gamma, g, h, tiles, coarse_ratio, **kw):
+    """U^0, W^0 after Step 1 and its causal sweep (eik_dd_shard_start, then
+    eik_dd_coarse_state) on the fine grid: NaN / 255 off the coarse set."""
+    grid = make_grid(r, h)
+    p = dd_params(tiles, coarse_ratio, **kw)
+    nbytes = eik_dd_workspace_size(grid, p)
+    if nbytes == 0:
+        raise EikError(-1, eik_last_error())
+    ws = _workspace(nbytes, r.device)
+    u = torch.empty_like(r)
+    eik_dd_shard_start(grid, r, gamma.contiguous(), g, p, u, ws)
+    Uc = torch.full_like(r, float("nan"))
+    Wc = torch.full(r.shape, 255, dtype=torch.uint8, device=r.device)
+    eik_dd_coarse_state(grid, p, ws, Uc, Wc)
+    return Uc, Wc
+
+
 def eik_dd_solve_noalloc(grid, r, gamma, g, params, u_out, stats_dev, stream=None):
     """eik_dd_solve with the library's static scratch instead of a workspace
     (for callers that cannot allocate device memory)."""
@@ -326,10 +353,12 @@ def fsm(r, gamma, g, h, max_sweeps=100000, stream=None, sync=True):
 
 
 def dd_solve(r, gamma, g, h, tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.0, max_fsm_sweeps=100000,
-             max_coarse_sweeps=8, stream=None, sync=True, **adaptive):
+             max_coarse_sweeps=8, stream=None, sync=True, return_coarse=False, **adaptive):
     """Two-scale DD solve (Sec. 3.2; Sec. 3.1 for a 1-D r, where tiles =
     (N,) subintervals and coarse_ratio must be their width M).  Returns (u,
-    stats dict).  Keyword
+    stats dict), and with return_coarse (2-D) also the coarse state the solve
+    leaves (eik_dd_coarse_state: U^k, or u^k at weight 0, and W = w^k) on the
+    fine grid.  Keyword
     arguments theta_adaptive, omega, sig_gamma, sig_delta, sig_x0, theta_cap
     select the per-node weight of Sec. 4.2 (see dd_params)."""
     _check_like(r, g)
@@ -344,12 +373,20 @@ def dd_solve(r, gamma, g, h, tiles, coarse_ratio, theta=1.0, max_iter=10, tol=0.
     u = torch.empty_like(r)
     st = torch.zeros(ctypes.sizeof(DDStats), dtype=torch.uint8, device=r.device)
     eik_dd_solve(grid, r, gamma.contiguous(), g, p, u, ws, st, stream)
+    coarse = ()
+    if return_coarse:
+        # the coarse state the workspace holds (U^k, or u^k at weight 0, and
+        # W = w^k) at the coarse-set nodes (NaN and 255 elsewhere)
+        Uc = torch.full_like(r, float("nan"))
+        Wc = torch.full(r.shape, 255, dtype=torch.uint8, device=r.device)
+        eik_dd_coarse_state(grid, p, ws, Uc, Wc, stream)
+        coarse = (Uc, Wc)
     if not sync:
-        return u, st
+        return (u, st) + coarse
     s = DDStats.from_buffer_copy(bytes(st.cpu().numpy()))
     if s.error:
         raise EikError(s.error, "device-side wait expired")
-    return u, _as_dict(s)
+    return (u, _as_dict(s)) + coarse
 
 
 def eik_dd_adjoint_workspace_size(grid: Grid) -> int:

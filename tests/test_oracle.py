@@ -438,3 +438,31 @@ def test_parallel_oracle_build_equals_serial():
     u0, s0, l0 = O.dd(r, gamma, g, h, (4, 4), 8, **kw)
     u1, s1, l1 = O.dd(r, gamma, g, h, (4, 4), 8, parallel=True, **kw)
     assert np.array_equal(u0, u1) and s0 == s1 and np.array_equal(l0, l1, equal_nan=True)
+
+
+def test_dd_margins_hooks_leave_the_method_unchanged():
+    """The test hooks of orc_dd_margins: without replacement the solution is
+    orc_dd's bitwise, replacing U^0 / W^0 by the solve's own changes nothing,
+    every coarse-set value of the first pass is one of the exported copies,
+    and a copy exists only on the coarse set; the Step 1 margins are defined
+    exactly on the coarse set and are never negative."""
+    n, h = 97, 1.0 / 96
+    r = I.sin_product((n, n), h, 0.5, 0.25)
+    gam, g = I.point_source((n, n), (32, 64))  # a coarse node: every shifted grid sees it
+    kw = dict(theta=0.0, max_coarse_sweeps=8)
+    u, st, W0, mg, cp, cm = O.dd_margins(r, gam, g, h, (3, 3), 8, max_iter=0, **kw)
+    u_ref, st_ref, _, U_ref = O.dd(r, gam, g, h, (3, 3), 8, max_iter=0, return_coarse=True, **kw)
+    assert np.array_equal(u, u_ref) and st["fine_updates"] == st_ref["fine_updates"]
+    cs = np.zeros((n, n), bool)
+    cs[::8, :] = True
+    cs[:, ::8] = True
+    U0 = np.where(cs, U_ref, np.nan)  # max_iter = 0: the coarse state after Step 1
+    u2, _, W0b, _, _, _ = O.dd_margins(r, gam, g, h, (3, 3), 8, max_iter=0, U0=U0, W0=W0, **kw)
+    assert np.array_equal(u2, u) and np.array_equal(W0b, W0)
+    assert np.all(np.any(cp[:, cs] == u[cs], axis=0))
+    assert not np.any(np.isfinite(cp[:, ~cs]))
+    assert np.all(np.isnan(mg[~cs])) and not np.any(np.isnan(mg[cs])) and np.all(mg[cs] >= 0)
+    # a different W^0 changes the first pass (the hook is applied)
+    W0x = -W0
+    u3, _, _, _, _, _ = O.dd_margins(r, gam, g, h, (3, 3), 8, max_iter=0, U0=U0, W0=W0x, **kw)
+    assert not np.array_equal(u3, u)
