@@ -498,7 +498,8 @@ def main():
             "time_to_solution_ms": ms_per_step,
             "gcells_per_s": cells * world / (ms_per_step / 1e3) / 1e9,
             "dd_stats": {k: stats[k] for k in ("iters", "converged", "fsm_sweeps_max", "coarse_sweeps_max",
-                                              "fine_updates", "coarse_updates", "last_delta")},
+                                              "fine_updates", "coarse_updates", "last_delta",
+                                              "fine_solves_skipped")},
             "accuracy": acc,
             "equal_error": equal,
             "fsm_baseline_f32": fsm_line,
