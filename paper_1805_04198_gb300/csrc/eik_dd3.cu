@@ -38,6 +38,7 @@ struct DD3Geom {
 
 struct DevStats3 {
     unsigned long long fsm_sweeps_max, coarse_sweeps_max, fsm_caps, coarse_caps, fine_updates, coarse_updates;
+    unsigned long long fine_skips;
     int causal_rounds_max, err, iters, converged;
 };
 
@@ -60,6 +61,12 @@ struct DD3Args {
     int *chg;
     unsigned *bar;
     DevStats3 *st;
+    // Step 2 data of each subdomain's last solve in this call (the starting
+    // value of every face node and the coarse wind an inflow node echoes),
+    // [ntiles][face slots], and whether the subdomain has been solved
+    T *sig_u;
+    uint8_t *sig_w;
+    int *sig_ok;
     T theta, tol;
     // constant weight 0: Alg. 5 yields u^k at every node, Alg. 4 writes
     // U^{k+1} = u^k itself and Step 4 is not launched
@@ -300,6 +307,7 @@ __global__ void k3_init(DD3Args<T> A) {
         A.bar[0] = A.bar[1] = 0;
     }
     for (int k = threadIdx.x; k < A.max_iter + 2; k += blockDim.x) A.deltas[k] = k == 0 ? INFINITY : 0.0;
+    for (int t = threadIdx.x; t < A.G.T[0] * A.G.T[1] * A.G.T[2]; t += blockDim.x) A.sig_ok[t] = 0;
 }
 
 // one CTA row per shifted grid (blockIdx.y), threads over its nodes
@@ -457,6 +465,35 @@ __device__ __forceinline__ bool tile3_inflow(const DD3Args<T> &A, const int *l, 
     return in;
 }
 
+// Face slots of a subdomain box: the six face planes in the order x = 0,
+// x = S, y = 0, y = S, z = 0, z = S; a node on several faces takes the slot
+// of the first.  Returns -1 off the faces.
+__host__ __device__ inline int box3_face_slots(const int *S) {
+    const int m0 = S[0] + 1, m1 = S[1] + 1, m2 = S[2] + 1;
+    return 2 * (m1 * m2 + m0 * m2 + m0 * m1);
+}
+__device__ inline int box3_face_slot(const int *S, const int *l) {
+    const int m0 = S[0] + 1, m1 = S[1] + 1, m2 = S[2] + 1;
+    if (l[0] == 0) return l[1] + m1 * l[2];
+    if (l[0] == S[0]) return m1 * m2 + l[1] + m1 * l[2];
+    int off = 2 * m1 * m2;
+    if (l[1] == 0) return off + l[0] + m0 * l[2];
+    if (l[1] == S[1]) return off + m0 * m2 + l[0] + m0 * l[2];
+    off += 2 * m0 * m2;
+    if (l[2] == 0) return off + l[0] + m0 * l[1];
+    if (l[2] == S[2]) return off + m0 * m1 + l[0] + m0 * l[1];
+    return -1;
+}
+
+template <class T>
+__device__ __forceinline__ bool same_bits3(T a, T b);
+template <>
+__device__ __forceinline__ bool same_bits3<float>(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+template <>
+__device__ __forceinline__ bool same_bits3<double>(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
 template <class T>
 __global__ void __launch_bounds__(BOX3_THREADS, 1) k3_fine(DD3Args<T> A) {
     if (*A.done) return;
@@ -472,7 +509,15 @@ __global__ void __launch_bounds__(BOX3_THREADS, 1) k3_fine(DD3Args<T> A) {
     uint8_t *fx = reinterpret_cast<uint8_t *>(su + (size_t)mz * ps);
     const int b0 = t0 * G.S[0], b1 = t1 * G.S[1], b2 = t2 * G.S[2];
     // Step 2: boundary data; inflow nodes start at U (and are swept like the
-    // rest), interior and outflow nodes at +inf; Gamma is fixed at g
+    // rest), interior and outflow nodes at +inf; Gamma is fixed at g.  The
+    // face nodes' data are compared with those of the subdomain's previous
+    // solve in this call: if none changed, that solve's results (fine values,
+    // copies) are still in place and equal bit for bit to what this one would
+    // write (r, Gamma and g do not change within a call), so it is skipped.
+    const int nslot = box3_face_slots(G.S);
+    T *sgu = A.sig_u + (size_t)tile * nslot;
+    uint8_t *sgw = A.sig_w + (size_t)tile * nslot;
+    bool diff = false;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int l[3] = {e % mx, (e / mx) % my, e / (mx * my)};
         const int Xg[3] = {b0 + l[0], b1 + l[1], b2 + l[2]};
@@ -490,7 +535,23 @@ __global__ void __launch_bounds__(BOX3_THREADS, 1) k3_fine(DD3Args<T> A) {
         const int q = l[2] * ps + l[1] * mx + l[0];
         su[q] = v;
         fx[q] = fixed;
+        const int fs = box3_face_slot(G.S, l);
+        if (fs >= 0) {
+            const T sv = fixed ? v : INF;
+            const uint8_t swv = fixed == 2 ? A.W[ca] : (uint8_t)0;
+            if (!same_bits3(sv, sgu[fs]) || swv != sgw[fs]) {
+                diff = true;
+                sgu[fs] = sv;
+                sgw[fs] = swv;
+            }
+        }
     }
+    const bool solved = A.sig_ok[tile] != 0;
+    if (!__syncthreads_or(diff) && solved) {
+        if (threadIdx.x == 0) atomicAdd(&A.st->fine_skips, 1ull);
+        return;
+    }
+    if (threadIdx.x == 0) A.sig_ok[tile] = 1;
     __syncthreads();
     Fsm3<T> pol{fx, A.r, (long long)fidx(A, b0, b1, b2), 1, A.sy, A.sz, T(G.h)};
     long long sweeps;
@@ -753,7 +814,7 @@ __global__ void k3_finalize(DD3Args<T> A, eik_dd_stats *out, long long launches)
     out->fine_updates = (int64_t)A.st->fine_updates;
     out->coarse_updates = (int64_t)A.st->coarse_updates;
     out->launches = launches;
-    out->fine_solves_skipped = 0;
+    out->fine_solves_skipped = (int64_t)A.st->fine_skips;
 }
 
 // --------------------------------------------------------------------------
@@ -828,6 +889,10 @@ static size_t dd3_layout(const DD3Plan &P, DD3Args<T> *A, void *ws, int max_iter
     int *chg = cv.take<int>(4);
     unsigned *bar = cv.take<unsigned>(4);
     DevStats3 *st = cv.take<DevStats3>(1);
+    const size_t ntl = (size_t)G.T[0] * G.T[1] * G.T[2], nsl = (size_t)box3_face_slots(G.S);
+    T *sig_u = cv.take<T>(ntl * nsl);
+    uint8_t *sig_w = cv.take<uint8_t>(ntl * nsl);
+    int *sig_ok = cv.take<int>(ntl);
     T *Ch[4] = {nullptr, nullptr, nullptr, nullptr}, *th = nullptr;
     double *du = nullptr;
     if (P.adaptive) {
@@ -843,6 +908,9 @@ static size_t dd3_layout(const DD3Plan &P, DD3Args<T> *A, void *ws, int max_iter
         A->W = W; A->wk = wk; A->mask = mask; A->cu = cu; A->cw = cw;
         A->grids = grids; A->offmap = offmap; A->done = done; A->deltas = deltas; A->chg = chg; A->bar = bar;
         A->st = st;
+        A->sig_u = sig_u;
+        A->sig_w = sig_w;
+        A->sig_ok = sig_ok;
     }
     return cv.used + 256;
 }
