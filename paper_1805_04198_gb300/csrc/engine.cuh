@@ -35,6 +35,8 @@
 // come for free: missing neighbours are +inf.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace eik {
@@ -163,6 +165,7 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
     const int pc = SX > 0 ? lane : 31 - lane;       // physical column in the block
     const int x = 32 * b + pc;
     const bool colok = x < NX;
+    const bool fullblk = 32 * b + 31 < NX;  // every lane of the block on a column
     const int bp = b - SX, bn = b + SX;              // physical predecessor / successor
     const bool has_prev = bp >= 0 && bp < NB;
     const bool has_next = bn >= 0 && bn < NB;
@@ -318,35 +321,44 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
         hal = halo[(s0 - lane) & (RROWS - 1)];
         const T *sbase = sring + (size_t)((J % SRCH) * CH) * 32 + lane;
         const uint8_t *bbase = sbring + ((J % SRCH) * CH) * 32 + lane;
+        // The chunk's 8 steps.  STEADY: every lane of a full block is on a
+        // valid row at every step and so is the row two ahead that it loads,
+        // so the row and column tests are dropped (the same operations on the
+        // same values otherwise).
+        auto run_chunk = [&](auto steady_tag) {
+            constexpr bool STEADY = decltype(steady_tag)::value;
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            const int m = s0 + i - lane;
-            const bool rowok = (unsigned)m < (unsigned)NY;
-            const bool act = colok && rowok;
-            // loads for the next step, issued before this step's store
-            const T dn2 = ringval(m + 2);
-            const T hal2 = halo[(m + 1) & (RROWS - 1)];
-            T sv[NST > 0 ? NST : 1];
+            for (int i = 0; i < CH; ++i) {
+                const int m = s0 + i - lane;
+                const bool rowok = STEADY || (unsigned)m < (unsigned)NY;
+                const bool act = STEADY || (colok && rowok);
+                // loads for the next step, issued before this step's store
+                const T dn2 = STEADY ? myring[((m + 2) & (RROWS - 1)) * 32] : ringval(m + 2);
+                const T hal2 = halo[(m + 1) & (RROWS - 1)];
+                T sv[NST > 0 ? NST : 1];
 #pragma unroll
-            for (int kk = 0; kk < NST; ++kk) sv[kk] = sbase[((size_t)kk * SRCH * CH + i) * 32];
-            const uint8_t sbv = HASB ? bbase[i * 32] : (uint8_t)0;
-            const T hin = __shfl_sync(FULL, hcur, i);
-            const T fromleft = __shfl_up_sync(FULL, last, 1);
-            const T fromright = __shfl_down_sync(FULL, dnx, 1);
-            const T left = lane0 ? ((has_prev && rowok) ? hin : INF) : fromleft;
-            const T right = lane31 ? ((nextok && rowok) ? hal : INF) : fromright;
-            bool ch = false;
-            const T upd = pol.update(cur, SX > 0 ? left : right, SX > 0 ? right : left, SY > 0 ? last : dnx,
-                                     SY > 0 ? dnx : last, sv, sbv, ch);
-            const T nw = act ? upd : INF;
-            changed = changed || (act && ch);
-            if (act) myring[(m & (RROWS - 1)) * 32] = nw;
-            if (act && lane31 && has_next) hand[m] = nw;
-            last = nw;
-            cur = dnx;
-            dnx = dn2;
-            hal = hal2;
-        }
+                for (int kk = 0; kk < NST; ++kk) sv[kk] = sbase[((size_t)kk * SRCH * CH + i) * 32];
+                const uint8_t sbv = HASB ? bbase[i * 32] : (uint8_t)0;
+                const T hin = __shfl_sync(FULL, hcur, i);
+                const T fromleft = __shfl_up_sync(FULL, last, 1);
+                const T fromright = __shfl_down_sync(FULL, dnx, 1);
+                const T left = lane0 ? ((has_prev && rowok) ? hin : INF) : fromleft;
+                const T right = lane31 ? ((nextok && rowok) ? hal : INF) : fromright;
+                bool ch = false;
+                const T upd = pol.update(cur, SX > 0 ? left : right, SX > 0 ? right : left, SY > 0 ? last : dnx,
+                                         SY > 0 ? dnx : last, sv, sbv, ch);
+                const T nw = act ? upd : INF;
+                changed = changed || (act && ch);
+                if (act) myring[(m & (RROWS - 1)) * 32] = nw;
+                if (act && lane31 && has_next) hand[m] = nw;
+                last = nw;
+                cur = dnx;
+                dnx = dn2;
+                hal = hal2;
+            }
+        };
+        if (fullblk && s0 >= 31 && s0 + CH + 1 < NY) run_chunk(std::true_type{});
+        else run_chunk(std::false_type{});
     }
     cp_async_wait<0>();
     fence<GLOBAL>();  // every lane's write-back before the block's completion flag
