@@ -55,6 +55,12 @@ struct DDArgs {
     T *sig_u;
     uint8_t *sig_w;
     int *sig_ok;
+    // order of the subdomain launch when a planning pass ran before it (null:
+    // CTA b solves tile0 + b and checks its own data): [ntiles] the
+    // subdomains that need a solve first, then the others; order_cnt [2]
+    // counts of both (reset by the stop test of each iteration)
+    int *order;
+    int *order_cnt;
     unsigned *bar;   // [2] grid barrier count / generation
     DevStats *st;
     T theta, tol;
@@ -604,9 +610,9 @@ __device__ bool tile_needs_solve(const DDArgs<T> &A, int tile) {
 }
 
 template <class T>
-__device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int tile) {
+__device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int tile, bool check = true) {
     if (*A.done) return;
-    if (!tile_needs_solve(A, tile)) {
+    if (check && !tile_needs_solve(A, tile)) {
         if (threadIdx.x == 0) atomicAdd(&A.st->fine_skips, 1ull);
         return;
     }
@@ -882,6 +888,7 @@ __global__ void k_alg4(DDArgs<T> A, int k) {
 
 template <class T>
 __device__ void check_body(const DDArgs<T> &A, int k) {
+    if (A.order_cnt) A.order_cnt[0] = A.order_cnt[1] = 0;  // for the next planning pass
     if (*A.done) return;
     const double delta = A.deltas[k];
     const bool failed = A.st->err != DEV_OK;  // an expired wait: later stages would only repeat it
@@ -934,6 +941,7 @@ __device__ void init_body(const DDArgs<T> &A) {
     }
     for (int k = threadIdx.x; k < A.max_iter + 2; k += blockDim.x) A.deltas[k] = k == 0 ? INFINITY : 0.0;
     for (int t = threadIdx.x; t < A.G.tx * A.G.ty; t += blockDim.x) A.sig_ok[t] = 0;
+    if (threadIdx.x == 0 && A.order_cnt) A.order_cnt[0] = A.order_cnt[1] = 0;
 }
 
 template <class T>

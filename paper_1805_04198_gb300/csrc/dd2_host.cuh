@@ -48,6 +48,8 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
     T *sig_u = cv.take<T>(ntiles * tile_face_count(G));
     uint8_t *sig_w = cv.take<uint8_t>(ntiles * tile_face_count(G));
     int *sig_ok = cv.take<int>(ntiles);
+    int *order = cv.take<int>(ntiles);
+    int *order_cnt = cv.take<int>(2);
     unsigned *bar = cv.take<unsigned>(4);
     DevStats *st = cv.take<DevStats>(1);
     T *Ch[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -81,6 +83,8 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
         A->sig_u = sig_u;
         A->sig_w = sig_w;
         A->sig_ok = sig_ok;
+        A->order = order;
+        A->order_cnt = order_cnt;
         A->bar = bar;
         A->st = st;
     }

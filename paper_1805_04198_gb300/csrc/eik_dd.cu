@@ -49,14 +49,47 @@ EIK_KERNEL_PAIR(k_step1, 96, 168)
 EIK_KERNEL_PAIR(k_step4, 160, 168)
 EIK_KERNEL_PAIR(k_step4a, 160, 168)
 
-// Subdomain kernel: CTA b solves subdomain A.tile0 + b.
+// Planning pass of a subdomain launch over tiles [t0, t0 + ntl): which
+// subdomains' Step 2 data changed since their previous solve in this call
+// (tile_needs_solve, which also records the new data).  Those are listed
+// first in A.order, the rest after them, so that the CTAs with work are the
+// lowest-numbered ones and are spread one per SM while they are at most as
+// many as the SMs.  The order is the atomics' and does not matter: the
+// subdomain solves are independent.
+template <class T>
+__global__ void k_fine_plan(DDArgs<T> A, int t0, int ntl) {
+    if (*A.done) return;
+    const int tile = t0 + blockIdx.x;
+    const bool need = tile_needs_solve(A, tile);
+    if (threadIdx.x == 0) {
+        if (need) {
+            A.order[atomicAdd(A.order_cnt, 1)] = tile;
+        } else {
+            A.order[ntl - 1 - atomicAdd(A.order_cnt + 1, 1)] = tile;
+            atomicAdd(&A.st->fine_skips, 1ull);
+        }
+    }
+}
+
+// Subdomain kernel: with a plan, CTA b solves subdomain A.order[b] when b is
+// below the count of subdomains that need a solve; without one, CTA b
+// solves subdomain A.tile0 + b if its data changed.
+template <class T>
+__device__ __forceinline__ void k_fine_entry(const DDArgs<T> &A, char *smem) {
+    if (!A.order) {
+        k_fine_body<T>(A, smem, A.tile0 + blockIdx.x);
+        return;
+    }
+    if (*A.done || (int)blockIdx.x >= *(volatile const int *)A.order_cnt) return;
+    k_fine_body<T>(A, smem, A.order[blockIdx.x], false);
+}
 __global__ void __maxnreg__(96) k_fine_f32(DDArgs<float> A) {
     extern __shared__ __align__(16) char smem[];
-    k_fine_body<float>(A, smem, A.tile0 + blockIdx.x);
+    k_fine_entry<float>(A, smem);
 }
 __global__ void __maxnreg__(168) k_fine_f64(DDArgs<double> A) {
     extern __shared__ __align__(16) char smem[];
-    k_fine_body<double>(A, smem, A.tile0 + blockIdx.x);
+    k_fine_entry<double>(A, smem);
 }
 
 template <class T> struct DDKernels;
@@ -250,9 +283,8 @@ struct DDSolve {
     // Steps 2-3 on subdomains [t0, t1)
     int fine(int t0, int t1) {
         if (t1 <= t0) return EIK_OK;
-        DDArgs<T> B = A;
-        B.tile0 = t0;
-        EIK_LAUNCH("dd_fine_subdomains", s, DDKernels<T>::fine<<<t1 - t0, fine_threads, fine_smem, s>>>(B)); ++nl;
+        EIK_LAUNCH("dd_fine_plan", s, k_fine_plan<T><<<t1 - t0, 256, 0, s>>>(A, t0, t1 - t0)); ++nl;
+        EIK_LAUNCH("dd_fine_subdomains", s, DDKernels<T>::fine<<<t1 - t0, fine_threads, fine_smem, s>>>(A)); ++nl;
         return EIK_OK;
     }
 
