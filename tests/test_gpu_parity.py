@@ -582,3 +582,31 @@ def test_coarse_state_readback_fp64_bitwise(gpu, n, tiles, c, kmax):
     u, st, Uc, _ = gpu.dd_solve(*dev_args, max_iter=kmax, return_coarse=True, **kw)
     _, _, _, U_ref = O.dd(r, gamma, g, h, tiles, c, max_iter=kmax, return_coarse=True, **kw)
     np.testing.assert_array_equal(Uc.cpu().numpy()[cs], U_ref[cs])
+
+
+@pytest.mark.parametrize("dim,n,tiles,c,kmax", [
+    (2, 65, (4, 4), 8, 10),
+    (2, 97, (3, 3), 16, 10),
+    (3, 17, (2, 2, 2), 4, 8),
+])
+def test_skipped_subdomain_solves_keep_results_bitwise(gpu, dim, n, tiles, c, kmax):
+    """Subdomains whose Step 2 data did not change since their previous solve
+    in the call are not solved again (fine_solves_skipped): once the
+    iteration at weight 0 has settled, the solves are skipped, and the result
+    after every k stays FP64 bitwise the oracle's, which solves every
+    subdomain every time."""
+    if dim == 2:
+        r, gamma, g, h = _dd_case(n, tiles, c, src=(0, 0))
+    else:
+        r, gamma, g, h = _dd3_case(n, src=(0, 0, 0))
+    kw = dict(theta=0.0, tol=0.0, max_coarse_sweeps=16)
+    skipped = 0
+    for k in range(kmax + 1):
+        u_ref, s_ref, _ = O.dd(r, gamma, g, h, tiles, c, max_iter=k, **kw)
+        u, st = gpu.dd_solve(_t(r, torch.float64), _t(gamma, torch.uint8), _t(g, torch.float64), h, tiles, c,
+                             max_iter=k, **kw)
+        assert st["iters"] == s_ref["iters"] == k
+        np.testing.assert_array_equal(u.cpu().numpy(), u_ref, err_msg="k=%d" % k)
+        assert st["fine_updates"] <= s_ref["fine_updates"]
+        skipped = st["fine_solves_skipped"]
+    assert skipped > 0
