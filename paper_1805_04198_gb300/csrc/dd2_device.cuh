@@ -609,7 +609,7 @@ __device__ bool tile_needs_solve(const DDArgs<T> &A, int tile) {
     return need;
 }
 
-template <class T>
+template <class T, bool STEADY_PATH = true>
 __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int tile, bool check = true) {
     if (*A.done) return;
     if (check && !tile_needs_solve(A, tile)) {
@@ -652,7 +652,7 @@ __device__ __forceinline__ void k_fine_body(const DDArgs<T> &A, char *smem, int 
     FsmPolicy<T> pol{T(G.h)};
     long long sweeps;
     bool conv;
-    engine_run<T, 1, false>(bx, pol, A.max_fsm, smem, sweeps, conv, &A.st->err);
+    engine_run<T, 1, false, false, STEADY_PATH>(bx, pol, A.max_fsm, smem, sweeps, conv, &A.st->err);
     if (threadIdx.x == 0) {
         atomicMax(&A.st->fsm_sweeps_max, (unsigned long long)sweeps);
         if (!conv) atomicAdd(&A.st->fsm_caps, 1ull);

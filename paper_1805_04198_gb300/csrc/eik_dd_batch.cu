@@ -254,7 +254,14 @@ __global__ void kb_causal(const DDArgs<T> *__restrict__ args, Segs hl, Segs vl, 
 EIK_BATCH_PAIR(kb_step1, k_step1_body, 96, 168)
 EIK_BATCH_PAIR(kb_step4, k_step4_body, 160, 168)
 EIK_BATCH_PAIR(kb_step4a, k_step4a_body, 160, 168)
-EIK_BATCH_PAIR(kb_fine, k_fine_body, 96, 168)
+// The batch's subdomains are small (17-65 nodes a side): chunks in which every
+// lane is on a valid row are rare there, and the engine's second copy of the
+// step for them made the batch's subdomain stage 16% slower, so it is left out.
+template <class T>
+__device__ __forceinline__ void kb_fine_body(const DDArgs<T> &A, char *smem, int tile) {
+    k_fine_body<T, false>(A, smem, tile);
+}
+EIK_BATCH_PAIR(kb_fine, kb_fine_body, 96, 168)
 
 template <class T> struct BatchKernels;
 template <> struct BatchKernels<float> {

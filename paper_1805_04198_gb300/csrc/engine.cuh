@@ -153,7 +153,7 @@ __device__ __forceinline__ bool wait_ge(const int *p, int target, const EngineCt
 
 // One sweep (number k, direction (SX, SY)) of physical block b by its warp.
 // Returns -1 if the engine is stopping, else whether any node changed.
-template <int SX, int SY, bool GLOBAL, class T, int NST, bool HASB, class P>
+template <int SX, int SY, bool GLOBAL, class T, int NST, bool HASB, bool STEADY_PATH, class P>
 __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *ring, T *sring, uint8_t *sbring,
                          T *halo, T *hand, const T *hands, size_t hand_elems, const EngineCtl &C, int *err) {
     using N = Num<T>;
@@ -357,8 +357,12 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
                 hal = hal2;
             }
         };
-        if (fullblk && s0 >= 31 && s0 + CH + 1 < NY) run_chunk(std::true_type{});
-        else run_chunk(std::false_type{});
+        if constexpr (STEADY_PATH) {
+            if (fullblk && s0 >= 31 && s0 + CH + 1 < NY) run_chunk(std::true_type{});
+            else run_chunk(std::false_type{});
+        } else {
+            run_chunk(std::false_type{});
+        }
     }
     cp_async_wait<0>();
     fence<GLOBAL>();  // every lane's write-back before the block's completion flag
@@ -374,7 +378,7 @@ __device__ int run_block(const Box<T, NST> &bx, const P &pol, int k, int b, T *r
 // columns live in `ghands` ([nb][ny] elements) and the control words in
 // `gctl` (engine_global_ints(nb) ints, zeroed before the launch); every CTA of
 // the grid must be co-resident (cooperative launch).  All threads must call it.
-template <class T, int NST, bool HASB, bool GLOBAL = false, class P>
+template <class T, int NST, bool HASB, bool GLOBAL = false, bool STEADY_PATH = true, class P>
 __device__ void engine_run(const Box<T, NST> &bx, const P &pol, long long max_sweeps, char *smem, long long &sweeps,
                            bool &converged, int *err, T *ghands = nullptr, int *gctl = nullptr, int cta = -1) {
     const int nwc = GLOBAL ? (int)(blockDim.x >> 5) : bx.nb;   // warps (blocks) of this CTA
@@ -434,10 +438,10 @@ __device__ void engine_run(const Box<T, NST> &bx, const P &pol, long long max_sw
             if (vload(C.abort_flag) || vload(C.stop_at) < k) break;
             int ch;
             switch (k & 3) {
-                case 0: ch = run_block<-1, -1, GLOBAL, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
-                case 1: ch = run_block<-1, +1, GLOBAL, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
-                case 2: ch = run_block<+1, -1, GLOBAL, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
-                default: ch = run_block<+1, +1, GLOBAL, T, NST, HASB>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                case 0: ch = run_block<-1, -1, GLOBAL, T, NST, HASB, STEADY_PATH>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                case 1: ch = run_block<-1, +1, GLOBAL, T, NST, HASB, STEADY_PATH>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                case 2: ch = run_block<+1, -1, GLOBAL, T, NST, HASB, STEADY_PATH>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
+                default: ch = run_block<+1, +1, GLOBAL, T, NST, HASB, STEADY_PATH>(bx, pol, k, b, ring, sring, sbring, halo, hand, hands, hand_e, C, err); break;
             }
             if (ch < 0) break;
             // sweep k of this block is complete: publish it, then the sweep status
