@@ -92,7 +92,7 @@ inline size_t dd_layout(const DDPlan &P, DDArgs<T> *A, void *ws, int max_iter) {
 }
 
 // Launch shape of a cooperative causal-sweep kernel: lines staged in shared
-// memory (one warp per line, up to 8 warps per CTA) when a line of lw nodes
+// memory (one warp per line, up to 2 warps per CTA) when a line of lw nodes
 // fits, else the in-place form with 8 warps per CTA.  blocks is capped by what
 // is co-resident so that the grid barrier cannot wait on an unscheduled CTA.
 struct CausalShape {
@@ -103,7 +103,10 @@ struct CausalShape {
 template <class T>
 inline int causal_shape(const void *kernel, int lw, int lines, int nsm, int smem_optin, CausalShape &cs) {
     const size_t wb = causal_warp_bytes<T>(lw);
-    int wpb = (int)std::min<size_t>(8, (size_t)std::max(0, smem_optin - 1024) / wb);
+    // two warps (lines) per CTA: the staged gathers of a line are many small
+    // loads, so lines spread over more SMs finish sooner (8 per CTA on 33 SMs:
+    // 7.8 ms of causal sweep on the 4097^2 solve; 2 per CTA on 129 SMs: 7.1 ms)
+    int wpb = (int)std::min<size_t>(2, (size_t)std::max(0, smem_optin - 1024) / wb);
     if (wpb >= 1) {
         cs.threads = 32 * wpb;
         cs.smem = (size_t)wpb * wb;
